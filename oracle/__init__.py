@@ -28,7 +28,7 @@ _lib = None
 # Defaults of the procedure's leaf parameters (expected samples per leaf and
 # the count above which a leaf is split once more).
 K_LEAF = 1024
-K_MAX = 4096
+K_MAX = 2048
 
 ERR_NAMES = {0: "ok", 1: "bad argument", 2: "out of range", 3: "capacity", 6: "internal"}
 

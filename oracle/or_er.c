@@ -173,17 +173,18 @@ int or_floyd_leaf(uint64_t L, uint64_t k, uint64_t seed, uint64_t node, uint64_t
 
 /* ---------------- tile tree inside one chunk ---------------- */
 
-/* Depth d of the tile tree: the smallest d with E <= k_leaf 2^d, where
- * E = m (U_c / N) is the chunk's expected sample count; it depends only on
- * (n, m, P), not on sampled counts. */
-static int tile_depth(uint64_t m, uint64_t Uc, u128 Ntot, uint32_t k_leaf, int *d_out)
+/* Depth d of the tile tree, one value for all chunks of an instance: the
+ * smallest d with E <= k_leaf 2^d, where E = m (U_nom / N) is the expected
+ * sample count of a chunk of the nominal (largest possible) universe U_nom.
+ * It depends only on (n, m, P), not on sampled counts. */
+static int tile_depth(uint64_t m, u128 Unom, u128 Ntot, uint32_t k_leaf, int *d_out)
 {
-    double E = (double)m * (or_dbl128((u128)Uc) / or_dbl128(Ntot));
+    double E = (double)m * (or_dbl128(Unom) / or_dbl128(Ntot));
     int d = 0;
     for (;;) {
         if (E <= (double)k_leaf * (double)((uint64_t)1 << d))
             break;
-        if (((u128)2 << d) > (u128)Uc)
+        if (((u128)2 << d) > Unom)
             break;
         if (d == OR_D_MAX)
             return 2;
@@ -250,17 +251,16 @@ static int tile_node(tile_ctx *c, int level, uint64_t j, uint64_t k)
     return 0;
 }
 
-/* All k_c sorted offsets of one chunk. */
-static int chunk_offsets(uint64_t seed, uint64_t chunk, uint64_t Uc, uint64_t m, u128 Ntot,
-                         uint32_t k_leaf, uint32_t k_max, uint64_t kc, uint64_t *offs)
+/* All k_c sorted offsets of one chunk with tile depth d. */
+static int chunk_offsets(uint64_t seed, uint64_t chunk, uint64_t Uc, int d, uint32_t k_max,
+                         uint64_t kc, uint64_t *offs)
 {
     tile_ctx c;
+    int rc;
     c.seed = seed;
     c.chunk = chunk;
     c.Uc = Uc;
-    int rc = tile_depth(m, Uc, Ntot, k_leaf, &c.d);
-    if (rc)
-        return rc;
+    c.d = d;
     c.W = (uint64_t)(((u128)Uc + (((u128)1 << c.d) - 1)) >> c.d);
     c.k_max = k_max;
     c.offs = offs;
@@ -332,12 +332,17 @@ int or_gnm_directed_chunk(uint64_t n, uint64_t m, uint64_t seed, uint32_t P, uin
     if (c >= P || k_leaf < 2 || k_max < k_leaf)
         return 1;
     u128 Ntot = (u128)n * (n - 1);
+    u128 Unom = (((u128)n + P - 1) / P) * (n - 1);
+    int d;
+    rc = tile_depth(m, Unom, Ntot, k_leaf, &d);
+    if (rc)
+        return rc;
     uint64_t r0 = row_bound(n, P, c), r1 = row_bound(n, P, (uint64_t)c + 1);
     uint64_t Uc = (r1 - r0) * (n - 1);
     uint64_t *offs = (uint64_t *)malloc((k_c ? k_c : 1) * sizeof(uint64_t));
     if (!offs)
         return 1;
-    rc = chunk_offsets(seed, c, Uc, m, Ntot, k_leaf, k_max, k_c, offs);
+    rc = chunk_offsets(seed, c, Uc, d, k_max, k_c, offs);
     if (!rc) {
         /* offset -> (u, v): row u = r0 + off / (n-1), column w = off mod (n-1)
          * with the diagonal skipped (no self-loops, Sec. 2). */
@@ -578,6 +583,10 @@ int or_gnm_undirected(uint64_t n, uint64_t m, uint64_t seed, uint32_t P, uint32_
         return 1;
     rc = or_gnm_undirected_chunk_counts(n, m, seed, P, cnt);
     u128 Ntot = tri_pairs(n);
+    u128 rmax = ((u128)n + P - 1) / P;
+    int d = 0;
+    if (!rc)
+        rc = tile_depth(m, rmax * rmax, Ntot, k_leaf, &d);
     edge_buf b = {0, 0, 0, 0};
     for (uint32_t i = 0; !rc && i < P; i++)
         for (uint32_t j = 0; !rc && j <= i; j++) {
@@ -588,7 +597,7 @@ int or_gnm_undirected(uint64_t n, uint64_t m, uint64_t seed, uint32_t P, uint32_
                 rc = 1;
                 break;
             }
-            rc = chunk_offsets(seed, (uint64_t)i * P + j, Uc, m, Ntot, k_leaf, k_max, kc, offs);
+            rc = chunk_offsets(seed, (uint64_t)i * P + j, Uc, d, k_max, kc, offs);
             for (uint64_t t = 0; !rc && t < kc; t++) {
                 uint64_t uu, vv;
                 und_map(n, P, i, j, offs[t], &uu, &vv);
