@@ -1,0 +1,161 @@
+/*
+ * kg.h -- C ABI of the GB300 communication-free Erdos-Renyi generators.
+ *
+ * Implements the generators of "Communication-free Massively Distributed
+ * Graph Generation" (Funke, Lamm, Meyer, Penschuck, Sanders, Schulz, Strash,
+ * von Looz): directed G(n,m) (Sec. 4.1), undirected G(n,m) (Sec. 4.2) and
+ * G(n,p) (Sec. 4.3), all built on the divide-and-conquer sampling of
+ * Sec. 2.2.  Every chunk of the adjacency matrix draws its random numbers from
+ * a counter-based generator keyed by (seed, chunk / subtree id), so the output
+ * is a pure function of (n, m or p, seed, chunks): the same call always
+ * returns the same bytes, however the GPU schedules the work.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Vertices are 0 .. n-1.  Simple graphs only: no self-loops, no parallel
+ *    edges (Sec. 2).
+ *  - Output edges are interleaved pairs (u, v) of `id_bytes` bytes each
+ *    (id_bytes = 4: uint32 pairs, 8 bytes per edge, requires n <= 2^32;
+ *    id_bytes = 8: uint64 pairs, 16 bytes per edge), sorted by (u, v).
+ *    Undirected generators write every edge in both directions.
+ *  - d_* pointers are device pointers owned by the caller; the library keeps
+ *    none of them after the call.  Scratch memory is taken from and returned
+ *    to the stream-ordered pool of the current device (cudaMallocAsync).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous: they enqueue kernels and return.
+ *  - Argument errors are reported synchronously and nothing is enqueued.
+ *    Errors found on the device (capacity, internal limits) set a per-device
+ *    error word that kg_last_error() reads; nothing is ever written beyond
+ *    cap_edges entries of d_out.
+ *  - `chunks` is P of the paper: the number of row chunks (directed) or the
+ *    side of the triangular P x P chunk matrix (undirected).  Changing P
+ *    changes which graph is drawn but not the distribution.
+ */
+#ifndef KG_H
+#define KG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum kg_status {
+  KG_OK = 0,
+  KG_ERR_ARG = 1,      /* invalid argument (reported before any work) */
+  KG_ERR_RANGE = 2,    /* valid but beyond the supported sizes */
+  KG_ERR_CAPACITY = 3, /* output buffer too small */
+  KG_ERR_CUDA = 4,     /* a CUDA call failed */
+  KG_ERR_TIMEOUT = 5,  /* a bounded device wait ran out */
+  KG_ERR_INTERNAL = 6  /* an internal limit was reached (not expected) */
+} kg_status;
+
+/*
+ * Directed G(n,m), Sec. 4.1 (Theorem 1): m ordered pairs drawn uniformly
+ * without replacement from the n(n-1) pairs u != v.  The rows are cut into P
+ * chunks (chunk c = rows [floor(cn/P), floor((c+1)n/P))); the chunk sample
+ * counts come from a binary split tree of hypergeometric variates (Sec. 2.2);
+ * each chunk then refines its count over a tile tree and samples every tile
+ * with Floyd's algorithm.
+ *   n >= 1; 1 <= chunks <= min(n, 2^24); m <= n(n-1); m <= 2^44;
+ *   ceil(n/P)(n-1) < 2^64; cap_edges >= m.
+ * Writes exactly m pairs to d_out.
+ */
+kg_status kg_gnm_directed(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks, int id_bytes,
+                          void* d_out, uint64_t cap_edges, void* stream);
+
+/* Same with explicit leaf parameters: k_leaf = expected samples per tile
+ * (the base-case threshold of Sec. 2.2, >= 2), k_max = the count above which a
+ * tile is split once more (k_leaf <= k_max <= 2048).  kg_gnm_directed uses
+ * k_leaf = 1024, k_max = 2048.  Different values draw different graphs. */
+kg_status kg_gnm_directed_ex(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                             uint32_t k_leaf, uint32_t k_max, int id_bytes, void* d_out,
+                             uint64_t cap_edges, void* stream);
+
+/* Chunk sample counts of directed G(n,m) (the split tree alone):
+ * d_counts[c] for c < chunks (device, uint64). */
+kg_status kg_gnm_directed_chunk_counts(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                                       uint64_t* d_counts, void* stream);
+
+/* The edges of chunks [c_begin, c_end) of directed G(n,m) only -- what PE
+ * c_begin..c_end-1 of the paper generates, with no communication.
+ * d_counts: the full chunk-count array from kg_gnm_directed_chunk_counts.
+ * Writes sum(d_counts[c_begin..c_end)) pairs to d_out (the caller sizes
+ * cap_edges from the counts).  If d_chunk_digest is non-NULL it receives,
+ * per chunk of the range, the order-independent digest
+ *   sum over edges of splitmix64(u xor rotl64(v, 32))  (mod 2^64);
+ * if d_chunk_hist is non-NULL it receives, per chunk, 65 uint64 counters:
+ * the number of vertices of the chunk with out-degree 0..63 and >= 64. */
+kg_status kg_gnm_directed_range(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                                uint32_t c_begin, uint32_t c_end, const uint64_t* d_counts,
+                                int id_bytes, void* d_out, uint64_t cap_edges,
+                                uint64_t* d_chunk_digest, uint64_t* d_chunk_hist, void* stream);
+
+/*
+ * Undirected G(n,m), Sec. 4.2 (Theorem 2): m unordered pairs drawn uniformly
+ * without replacement.  The lower triangle of the adjacency matrix is cut
+ * into the triangular P x P chunk matrix; the quadrant recursion (split
+ * l = ceil(P/2), two triangles and one rectangle per triangle node) gives each
+ * chunk its count; chunk (i, j) draws from the stream of id i*P + j, the
+ * seed both PEs i and j of the paper share.
+ *   n >= 1; 1 <= chunks <= min(n, 2^16); m <= n(n-1)/2; m <= 2^44;
+ *   n <= 2^31; cap_edges >= 2m.
+ * Writes exactly 2m pairs (both directions).
+ */
+kg_status kg_gnm_undirected(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks, int id_bytes,
+                            void* d_out, uint64_t cap_edges, void* stream);
+kg_status kg_gnm_undirected_ex(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                               uint32_t k_leaf, uint32_t k_max, int id_bytes, void* d_out,
+                               uint64_t cap_edges, void* stream);
+
+/*
+ * G(n,p), Sec. 4.3: every pair independently with probability p, by
+ * geometric skips (Batagelj and Brandes, Sec. 3.1) over tiles of each chunk;
+ * a tile's skips come from the stream of (chunk id, tile), so the chunk law is
+ * fixed by its seed alone.  Directed pairs are ordered (E[m] = p n(n-1));
+ * undirected pairs are unordered (E[m] = p n(n-1)/2) and written both ways.
+ *   0 <= p <= 1; chunk limits as above (undirected: n <= 2^31).
+ * *d_count (device, uint64) receives the number of pairs written; if it
+ * exceeds cap_edges only the first cap_edges are written and the device
+ * error word becomes KG_ERR_CAPACITY.
+ */
+kg_status kg_gnp_directed(uint64_t n, double p, uint64_t seed, uint32_t chunks, int id_bytes,
+                          void* d_out, uint64_t cap_edges, uint64_t* d_count, void* stream);
+kg_status kg_gnp_undirected(uint64_t n, double p, uint64_t seed, uint32_t chunks, int id_bytes,
+                            void* d_out, uint64_t cap_edges, uint64_t* d_count, void* stream);
+/* As above with the tile parameter k_leaf (tile length = largest power of two
+ * <= max(1, k_leaf/p); default 1024). */
+kg_status kg_gnp_ex(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
+                    uint32_t k_leaf, int id_bytes, void* d_out, uint64_t cap_edges,
+                    uint64_t* d_count, void* stream);
+
+/* Order-independent digest of an edge list (see kg_gnm_directed_range):
+ * *d_digest = sum of splitmix64(u xor rotl64(v, 32)) over `count` pairs. */
+kg_status kg_edge_digest(const void* d_edges, uint64_t count, int id_bytes, uint64_t* d_digest,
+                         void* stream);
+
+/* Synchronises `stream`, returns and clears the current device's error word. */
+kg_status kg_last_error(void* stream);
+
+/* Human-readable name of a status. */
+const char* kg_status_str(kg_status s);
+
+/*
+ * Instrumentation (no counterpart in the paper).
+ * kg_launch_count: number of kernels this library has launched in the process.
+ * kg_profile_begin / kg_profile_end: while enabled, every launch is bracketed
+ * by a CUDA event pair recorded on the stream it is launched on; _end waits
+ * for those events and returns, per kernel class, the summed milliseconds and
+ * the number of launches (arrays of KG_PROF_CLASSES entries, host memory).
+ * Classes: 0 chunk split tree, 1 tile tree, 2 scan, 3 leaf sampler/emitter,
+ * 4 digest, 5 G(n,p) tile sampler, 6 undirected assembly, 7 other.
+ */
+#define KG_PROF_CLASSES 8
+unsigned long long kg_launch_count(void);
+kg_status kg_profile_begin(void);
+kg_status kg_profile_end(double* ms, unsigned long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KG_H */

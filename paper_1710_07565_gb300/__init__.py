@@ -1,0 +1,227 @@
+"""GB300-native communication-free Erdos-Renyi generators (directed / undirected
+G(n,m) and G(n,p)) -- Python binding of the C ABI in include/kg.h.
+
+Every function named ``kg_*`` here is argument marshalling for the C entry
+point of the same name in libkg.so: device pointers and streams are passed as
+integers, the work runs in the CUDA kernels.  The convenience wrappers
+(``gnm_directed`` ...) allocate the output with PyTorch (device memory only)
+and call the same entry points.  There is no CPU path: if the library cannot
+be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import _build_lib
+
+KG_OK, KG_ERR_ARG, KG_ERR_RANGE, KG_ERR_CAPACITY, KG_ERR_CUDA, KG_ERR_TIMEOUT, KG_ERR_INTERNAL = range(7)
+K_LEAF_DEFAULT = 1024
+K_MAX_DEFAULT = 2048
+
+_lock = threading.Lock()
+_lib = None
+
+
+class KGError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)} (status {status})")
+
+
+def build(force: bool = False) -> str:
+    """Compile libkg.so for sm_103a in-tree."""
+    return _build_lib.build(force=force)
+
+
+def lib_path() -> str:
+    return _build_lib.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """The loaded CUDA library (built on first use if the toolchain is present)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build_lib.LIB
+            if not os.path.exists(path):
+                path = _build_lib.build()
+            L = ctypes.CDLL(path)
+            u64, u32, i32, dbl, vp = (ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                      ctypes.c_double, ctypes.c_void_p)
+            sigs = {
+                "kg_gnm_directed": [u64, u64, u64, u32, i32, vp, u64, vp],
+                "kg_gnm_directed_ex": [u64, u64, u64, u32, u32, u32, i32, vp, u64, vp],
+                "kg_gnm_directed_chunk_counts": [u64, u64, u64, u32, vp, vp],
+                "kg_gnm_directed_range": [u64, u64, u64, u32, u32, u32, vp, i32, vp, u64, vp, vp, vp],
+                "kg_gnm_undirected": [u64, u64, u64, u32, i32, vp, u64, vp],
+                "kg_gnm_undirected_ex": [u64, u64, u64, u32, u32, u32, i32, vp, u64, vp],
+                "kg_gnp_directed": [u64, dbl, u64, u32, i32, vp, u64, vp, vp],
+                "kg_gnp_undirected": [u64, dbl, u64, u32, i32, vp, u64, vp, vp],
+                "kg_gnp_ex": [i32, u64, dbl, u64, u32, u32, i32, vp, u64, vp, vp],
+                "kg_edge_digest": [vp, u64, i32, vp, vp],
+                "kg_last_error": [vp],
+            }
+            for name, args in sigs.items():
+                f = getattr(L, name, None)
+                if f is None:
+                    continue
+                f.argtypes = args
+                f.restype = ctypes.c_int
+            L.kg_status_str.argtypes = [ctypes.c_int]
+            L.kg_status_str.restype = ctypes.c_char_p
+            L.kg_launch_count.argtypes = []
+            L.kg_launch_count.restype = ctypes.c_ulonglong
+            L.kg_profile_begin.argtypes = []
+            L.kg_profile_begin.restype = ctypes.c_int
+            L.kg_profile_end.argtypes = [ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_ulonglong)]
+            L.kg_profile_end.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def status_str(status: int) -> str:
+    try:
+        return lib().kg_status_str(status).decode()
+    except OSError:
+        return f"status {status}"
+
+
+def _call(name, *args):
+    st = getattr(lib(), name)(*args)
+    if st != KG_OK:
+        raise KGError(st, name)
+    return st
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+# ---------------------------------------------------------------- raw entry points
+
+def kg_gnm_directed(n, m, seed, chunks, id_bytes, d_out, cap_edges, stream):
+    return _call("kg_gnm_directed", n, m, seed, chunks, id_bytes, d_out, cap_edges, stream)
+
+
+def kg_gnm_directed_ex(n, m, seed, chunks, k_leaf, k_max, id_bytes, d_out, cap_edges, stream):
+    return _call("kg_gnm_directed_ex", n, m, seed, chunks, k_leaf, k_max, id_bytes, d_out,
+                 cap_edges, stream)
+
+
+def kg_gnm_directed_chunk_counts(n, m, seed, chunks, d_counts, stream):
+    return _call("kg_gnm_directed_chunk_counts", n, m, seed, chunks, d_counts, stream)
+
+
+def kg_gnm_directed_range(n, m, seed, chunks, c_begin, c_end, d_counts, id_bytes, d_out,
+                          cap_edges, d_chunk_digest, d_chunk_hist, stream):
+    return _call("kg_gnm_directed_range", n, m, seed, chunks, c_begin, c_end, d_counts, id_bytes,
+                 d_out, cap_edges, d_chunk_digest, d_chunk_hist, stream)
+
+
+def kg_gnm_undirected(n, m, seed, chunks, id_bytes, d_out, cap_edges, stream):
+    return _call("kg_gnm_undirected", n, m, seed, chunks, id_bytes, d_out, cap_edges, stream)
+
+
+def kg_gnm_undirected_ex(n, m, seed, chunks, k_leaf, k_max, id_bytes, d_out, cap_edges, stream):
+    return _call("kg_gnm_undirected_ex", n, m, seed, chunks, k_leaf, k_max, id_bytes, d_out,
+                 cap_edges, stream)
+
+
+def kg_gnp_directed(n, p, seed, chunks, id_bytes, d_out, cap_edges, d_count, stream):
+    return _call("kg_gnp_directed", n, p, seed, chunks, id_bytes, d_out, cap_edges, d_count, stream)
+
+
+def kg_gnp_undirected(n, p, seed, chunks, id_bytes, d_out, cap_edges, d_count, stream):
+    return _call("kg_gnp_undirected", n, p, seed, chunks, id_bytes, d_out, cap_edges, d_count,
+                 stream)
+
+
+def kg_gnp_ex(undirected, n, p, seed, chunks, k_leaf, id_bytes, d_out, cap_edges, d_count, stream):
+    return _call("kg_gnp_ex", int(undirected), n, p, seed, chunks, k_leaf, id_bytes, d_out,
+                 cap_edges, d_count, stream)
+
+
+def kg_edge_digest(d_edges, count, id_bytes, d_digest, stream):
+    return _call("kg_edge_digest", d_edges, count, id_bytes, d_digest, stream)
+
+
+def kg_last_error(stream) -> int:
+    return lib().kg_last_error(stream)
+
+
+PROF_CLASSES = ("chunk_tree", "tile_tree", "scan", "leaf", "digest", "gnp_tile", "assembly", "other")
+
+
+def kg_launch_count() -> int:
+    return lib().kg_launch_count()
+
+
+def kg_profile_begin():
+    return _call("kg_profile_begin")
+
+
+def kg_profile_end():
+    """{class: (milliseconds, launches)} of the launches since kg_profile_begin."""
+    ms = (ctypes.c_double * len(PROF_CLASSES))()
+    n = (ctypes.c_ulonglong * len(PROF_CLASSES))()
+    st = lib().kg_profile_end(ms, n)
+    if st != KG_OK:
+        raise KGError(st, "kg_profile_end")
+    return {c: (ms[i], n[i]) for i, c in enumerate(PROF_CLASSES)}
+
+
+# ---------------------------------------------------------------- torch helpers
+
+def _empty_edges(count, id_bytes, device):
+    import torch
+    dt = torch.int32 if id_bytes == 4 else torch.int64
+    return torch.empty((max(count, 1), 2), dtype=dt, device=device)
+
+
+def check_device_error(stream=None):
+    st = kg_last_error(_stream_ptr(stream))
+    if st != KG_OK:
+        raise KGError(st, "device")
+
+
+def gnm_directed(n, m, seed=1, chunks=1, id_bytes=4, k_leaf=K_LEAF_DEFAULT, k_max=K_MAX_DEFAULT,
+                 out=None, stream=None, device="cuda"):
+    """Directed G(n,m) as an (m, 2) int32/int64 tensor of (u, v) (int32 holds uint32 bits)."""
+    if out is None:
+        out = _empty_edges(m, id_bytes, device)
+    kg_gnm_directed_ex(n, m, seed, chunks, k_leaf, k_max, id_bytes, out.data_ptr(), m,
+                       _stream_ptr(stream))
+    return out[:m]
+
+
+def gnm_undirected(n, m, seed=1, chunks=1, id_bytes=4, k_leaf=K_LEAF_DEFAULT, k_max=K_MAX_DEFAULT,
+                   out=None, stream=None, device="cuda"):
+    """Undirected G(n,m) as a (2m, 2) tensor: both directions, sorted by (u, v)."""
+    if out is None:
+        out = _empty_edges(2 * m, id_bytes, device)
+    kg_gnm_undirected_ex(n, m, seed, chunks, k_leaf, k_max, id_bytes, out.data_ptr(), 2 * m,
+                         _stream_ptr(stream))
+    return out[:2 * m]
+
+
+def gnp(undirected, n, p, seed=1, chunks=1, id_bytes=4, k_leaf=K_LEAF_DEFAULT, cap=None,
+        stream=None, device="cuda"):
+    """G(n,p) edge list; returns (edges tensor view, device count tensor)."""
+    import torch
+    if cap is None:
+        pairs = n * (n - 1) // (2 if undirected else 1)
+        mean = pairs * p
+        cap = int(min(pairs, mean + 12 * (mean ** 0.5) + 64)) * (2 if undirected else 1)
+    out = _empty_edges(cap, id_bytes, device)
+    cnt = torch.zeros(1, dtype=torch.int64, device=device)
+    kg_gnp_ex(undirected, n, p, seed, chunks, k_leaf, id_bytes, out.data_ptr(), cap, cnt.data_ptr(),
+              _stream_ptr(stream))
+    return out, cnt

@@ -1,0 +1,260 @@
+// C ABI: directed G(n,m) (Sec. 4.1), its chunk counts and chunk ranges, the
+// edge digest, and the status / error-word plumbing shared by all entry points.
+#include <mutex>
+#include <unordered_map>
+
+#include "../../include/kg.h"
+#include "kg_digest.cuh"
+#include "kg_gnm.cuh"
+#include "kg_internal.h"
+#include "kg_prof.h"
+
+namespace kg {
+
+// ---------------------------------------------------------------- error word, pool
+int* device_error_word() {
+  static std::mutex mu;
+  static std::unordered_map<int, int*> words;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = words.find(dev);
+  if (it != words.end()) return it->second;
+  int* p = nullptr;
+  if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) return nullptr;
+  if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return nullptr;
+  // keep freed scratch cached in the device's stream-ordered pool
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~uint64_t(0);
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  words[dev] = p;
+  return p;
+}
+
+// Tile-tree depth, one per instance: smallest d with E <= k_leaf 2^d, where
+// E = m (U_nom / N) is the expected count of a chunk of nominal universe U_nom.
+int tile_depth(uint64_t m, u128 Unom, u128 Ntot, uint32_t k_leaf, int& d_out) {
+  const double E = double(m) * (dbl(Unom) / dbl(Ntot));
+  int d = 0;
+  for (;;) {
+    if (E <= double(k_leaf) * double(uint64_t(1) << d)) break;
+    if ((u128(2) << d) > Unom) break;
+    if (d == D_MAX) return ST_RANGE;
+    ++d;
+  }
+  d_out = d;
+  return ST_OK;
+}
+
+static unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
+  uint64_t b = (items + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return unsigned(b);
+}
+
+static int launch_ok() { return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA; }
+
+// Tile trees + scan + leaves for chunks [c_begin, c_begin + C) of a geometry.
+// level0: the chunks' counts (device).  Pairs go to d_out[0 ..).
+template <class Geom>
+int run_chunks(const Geom& g, uint64_t c_begin, uint64_t C, const uint64_t* level0, int d,
+               uint32_t k_max, uint64_t seed, int id_bytes, void* d_out, uint64_t cap,
+               Workspace& ws, cudaStream_t s, int* err) {
+  const uint64_t T = C << d;
+  const uint64_t* in = level0;
+  if (d > 0) {
+    uint64_t* A = ws.alloc<uint64_t>(T);
+    uint64_t* B = ws.alloc<uint64_t>(T);
+    if (!ws.ok()) return ST_CUDA;
+    for (int level = 0; level < d; ++level) {
+      uint64_t* out = (level & 1) ? B : A;
+      const uint64_t nodes = C << level;
+      ProfScope ps(PROF_TILE_TREE, s);
+      tile_tree_level<Geom><<<grid_for(nodes, 8, 152 * 128), 256, 0, s>>>(
+          g, c_begin, C, d, level, seed, in, out, err);
+      if (launch_ok()) return ST_CUDA;
+      in = out;
+    }
+  }
+  uint64_t* tile_off = ws.alloc<uint64_t>(T + 1);
+  if (!ws.ok()) return ST_CUDA;
+  int st = scan_exclusive_u64(in, tile_off, T, ws, s);
+  if (st) return st;
+  const unsigned grid = unsigned(T < 0x7fffffffull ? T : 0x7fffffffull);
+  ProfScope ps(PROF_LEAF, s);
+  if (id_bytes == 4) {
+    PairSink<uint32_t> sink{static_cast<uint32_t*>(d_out), cap, err};
+    leaf_kernel<Geom, PairSink<uint32_t>><<<grid, LEAF_THREADS, 0, s>>>(
+        g, sink, c_begin, d, k_max, seed, in, tile_off, T, err);
+  } else {
+    PairSink<uint64_t> sink{static_cast<uint64_t*>(d_out), cap, err};
+    leaf_kernel<Geom, PairSink<uint64_t>><<<grid, LEAF_THREADS, 0, s>>>(
+        g, sink, c_begin, d, k_max, seed, in, tile_off, T, err);
+  }
+  return launch_ok();
+}
+
+// ---------------------------------------------------------------- directed
+struct DirParams {
+  uint64_t n, m;
+  uint32_t P;
+  u128 Ntot, Unom;
+  int d, D;  // tile depth, chunk-tree depth ceil(log2 P)
+};
+
+static int check_directed(uint64_t n, uint64_t m, uint32_t P, uint32_t k_leaf, uint32_t k_max,
+                          int id_bytes, DirParams& dp) {
+  if (n == 0 || P == 0 || uint64_t(P) > n) return ST_ARG;
+  if (id_bytes != 4 && id_bytes != 8) return ST_ARG;
+  if (k_leaf < 2 || k_max < k_leaf || k_max > uint32_t(K_MAX)) return ST_ARG;
+  dp.n = n;
+  dp.m = m;
+  dp.P = P;
+  dp.Ntot = u128(n) * (n - 1);
+  if (u128(m) > dp.Ntot) return ST_ARG;
+  if (m > M_MAX) return ST_RANGE;
+  if (P > (1u << 24)) return ST_RANGE;
+  if (id_bytes == 4 && n > (uint64_t(1) << 32)) return ST_RANGE;
+  const uint64_t rows_max = uint64_t((u128(n) + P - 1) / P);
+  dp.Unom = u128(rows_max) * (n - 1);
+  if (dp.Unom >> 64) return ST_RANGE;
+  int st = tile_depth(m, dp.Unom, dp.Ntot, k_leaf, dp.d);
+  if (st) return st;
+  dp.D = 0;
+  while ((uint64_t(1) << dp.D) < P) ++dp.D;
+  return ST_OK;
+}
+
+static DirGeom dir_geom(uint64_t n, uint32_t P) {
+  DirGeom g;
+  g.n = n;
+  g.P = P;
+  g.div = make_div(n > 1 ? n - 1 : 1);
+  return g;
+}
+
+// Chunk split tree: bands of 8 levels, one block per subtree root.
+static int run_chunk_tree(const DirParams& dp, uint64_t seed, uint64_t* cnt, Workspace& ws,
+                          cudaStream_t s, int* err) {
+  uint64_t* node_cnt = ws.alloc<uint64_t>(uint64_t(2) << dp.D);
+  if (!ws.ok()) return ST_CUDA;
+  for (int l0 = 0; l0 <= dp.D; l0 += 8) {
+    const int l1 = (l0 + 8 < dp.D + 1) ? l0 + 8 : dp.D + 1;
+    ProfScope ps(PROF_CHUNK_TREE, s);
+    chunk_tree_band<<<unsigned(1) << l0, 256, 0, s>>>(dp.n, dp.P, seed, dp.m, l0, l1, node_cnt, cnt,
+                                                       err);
+    if (launch_ok()) return ST_CUDA;
+  }
+  return ST_OK;
+}
+
+}  // namespace kg
+
+using namespace kg;
+
+static cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+const char* kg_status_str(kg_status s) {
+  switch (s) {
+    case KG_OK: return "ok";
+    case KG_ERR_ARG: return "invalid argument";
+    case KG_ERR_RANGE: return "size out of supported range";
+    case KG_ERR_CAPACITY: return "output capacity too small";
+    case KG_ERR_CUDA: return "CUDA error";
+    case KG_ERR_TIMEOUT: return "device wait timed out";
+    case KG_ERR_INTERNAL: return "internal limit reached";
+  }
+  return "unknown status";
+}
+
+kg_status kg_last_error(void* stream) {
+  int* err = device_error_word();
+  if (!err) return KG_ERR_CUDA;
+  if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return KG_ERR_CUDA;
+  int h = 0;
+  if (cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return KG_ERR_CUDA;
+  if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess) return KG_ERR_CUDA;
+  return kg_status(h);
+}
+
+kg_status kg_gnm_directed_chunk_counts(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                                       uint64_t* d_counts, void* stream) {
+  DirParams dp;
+  int st = check_directed(n, m, chunks, K_LEAF, K_MAX, 8, dp);
+  if (st) return kg_status(st);
+  if (!d_counts) return KG_ERR_ARG;
+  int* err = device_error_word();
+  if (!err) return KG_ERR_CUDA;
+  Workspace ws(as_stream(stream));
+  return kg_status(run_chunk_tree(dp, seed, d_counts, ws, as_stream(stream), err));
+}
+
+kg_status kg_gnm_directed_ex(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                             uint32_t k_leaf, uint32_t k_max, int id_bytes, void* d_out,
+                             uint64_t cap_edges, void* stream) {
+  DirParams dp;
+  int st = check_directed(n, m, chunks, k_leaf, k_max, id_bytes, dp);
+  if (st) return kg_status(st);
+  if (cap_edges < m) return KG_ERR_CAPACITY;
+  if (m == 0) return KG_OK;
+  if (!d_out) return KG_ERR_ARG;
+  int* err = device_error_word();
+  if (!err) return KG_ERR_CUDA;
+  cudaStream_t s = as_stream(stream);
+  Workspace ws(s);
+  uint64_t* cnt = ws.alloc<uint64_t>(chunks);
+  if (!ws.ok()) return KG_ERR_CUDA;
+  st = run_chunk_tree(dp, seed, cnt, ws, s, err);
+  if (st) return kg_status(st);
+  st = run_chunks(dir_geom(n, chunks), 0, chunks, cnt, dp.d, k_max, seed, id_bytes, d_out,
+                  cap_edges, ws, s, err);
+  return kg_status(st);
+}
+
+kg_status kg_gnm_directed(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks, int id_bytes,
+                          void* d_out, uint64_t cap_edges, void* stream) {
+  return kg_gnm_directed_ex(n, m, seed, chunks, K_LEAF, K_MAX, id_bytes, d_out, cap_edges, stream);
+}
+
+kg_status kg_gnm_directed_range(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                                uint32_t c_begin, uint32_t c_end, const uint64_t* d_counts,
+                                int id_bytes, void* d_out, uint64_t cap_edges,
+                                uint64_t* d_chunk_digest, uint64_t* d_chunk_hist, void* stream) {
+  DirParams dp;
+  int st = check_directed(n, m, chunks, K_LEAF, K_MAX, id_bytes, dp);
+  if (st) return kg_status(st);
+  if (c_begin > c_end || c_end > chunks || !d_counts) return KG_ERR_ARG;
+  const uint64_t C = c_end - c_begin;
+  if (C == 0) return KG_OK;
+  if (!d_out && cap_edges > 0) return KG_ERR_ARG;
+  int* err = device_error_word();
+  if (!err) return KG_ERR_CUDA;
+  cudaStream_t s = as_stream(stream);
+  Workspace ws(s);
+  const DirGeom g = dir_geom(n, chunks);
+  st = run_chunks(g, c_begin, C, d_counts + c_begin, dp.d, K_MAX, seed, id_bytes, d_out, cap_edges,
+                  ws, s, err);
+  if (st) return kg_status(st);
+  if (d_chunk_digest || d_chunk_hist) {
+    uint64_t* chunk_off = ws.alloc<uint64_t>(C + 1);
+    if (!ws.ok()) return KG_ERR_CUDA;
+    st = scan_exclusive_u64(d_counts + c_begin, chunk_off, C, ws, s);
+    if (st) return kg_status(st);
+    st = chunk_digest(g, c_begin, C, chunk_off, id_bytes, d_out, cap_edges, d_chunk_digest,
+                      d_chunk_hist, s);
+  }
+  return kg_status(st);
+}
+
+kg_status kg_edge_digest(const void* d_edges, uint64_t count, int id_bytes, uint64_t* d_digest,
+                         void* stream) {
+  if ((id_bytes != 4 && id_bytes != 8) || !d_digest || (count && !d_edges)) return KG_ERR_ARG;
+  return kg_status(edge_digest(d_edges, count, id_bytes, d_digest, as_stream(stream)));
+}
+
+}  // extern "C"

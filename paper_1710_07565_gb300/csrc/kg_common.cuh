@@ -1,0 +1,153 @@
+// Shared launch helpers, chunk geometries and block-level scans.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+
+#include "kg_device.cuh"
+
+namespace kg {
+
+constexpr int K_LEAF = 1024;  // expected samples per tile (base-case threshold)
+constexpr int K_MAX = 2048;   // a leaf with more samples is split once more
+constexpr int LEAF_THREADS = 256;
+
+__device__ __forceinline__ void set_error(int* err, int code) {
+  if (err) atomicCAS(err, 0, code);
+}
+
+// Chunk boundary r_c = floor(c n / P) ("sections of size roughly n/P", Sec. 4.2).
+__host__ __device__ __forceinline__ uint64_t row_bound(uint64_t n, uint32_t P, uint64_t c) {
+  return uint64_t((u128(c) * n) / P);
+}
+
+// Directed chunks (Sec. 4.1): chunk c = rows [r_c, r_{c+1}) x all n-1 columns
+// other than the row itself; offsets are row-major, the diagonal skipped.
+struct DirGeom {
+  uint64_t n;
+  uint32_t P;
+  DivU64 div;  // division by n-1
+
+  __host__ __device__ __forceinline__ uint64_t chunk_id(uint64_t c) const { return c; }
+  __host__ __device__ __forceinline__ uint64_t universe(uint64_t c) const {
+    return (row_bound(n, P, c + 1) - row_bound(n, P, c)) * (n - 1);
+  }
+  struct Ctx {
+    uint64_t r0;
+  };
+  __host__ __device__ __forceinline__ Ctx ctx(uint64_t c) const { return Ctx{row_bound(n, P, c)}; }
+  __host__ __device__ __forceinline__ void map(const Ctx& x, uint64_t off, uint64_t& u,
+                                               uint64_t& v) const {
+    const uint64_t q = div_q(div, off);
+    const uint64_t w = off - q * (n - 1);
+    u = x.r0 + q;
+    v = w + (w >= u ? 1 : 0);
+  }
+};
+
+// Undirected chunks (Sec. 4.2): chunk (i, j), j <= i, of the triangular P x P
+// chunk matrix; chunk index k enumerates (i, j) row by row, k = i(i+1)/2 + j,
+// and the chunk's stream id is i P + j.  Rectangles (i > j) are row-major,
+// triangles (i = j) hold u > v with offset (u-a)(u-a-1)/2 + (v-a).
+struct UndGeom {
+  uint64_t n;
+  uint32_t P;
+
+  __host__ __device__ __forceinline__ static void ij(uint64_t k, uint32_t& i, uint32_t& j) {
+    uint64_t r = uint64_t(sqrt(8.0 * double(k) + 1.0) - 1.0) / 2;
+    while (r * (r + 1) / 2 > k) --r;
+    while ((r + 1) * (r + 2) / 2 <= k) ++r;
+    i = uint32_t(r);
+    j = uint32_t(k - r * (r + 1) / 2);
+  }
+  __host__ __device__ __forceinline__ uint64_t chunk_id(uint64_t k) const {
+    uint32_t i, j;
+    ij(k, i, j);
+    return uint64_t(i) * P + j;
+  }
+  __host__ __device__ __forceinline__ uint64_t universe(uint64_t k) const {
+    uint32_t i, j;
+    ij(k, i, j);
+    const uint64_t si = row_bound(n, P, uint64_t(i) + 1) - row_bound(n, P, i);
+    if (i == j) return si ? uint64_t(u128(si) * (si - 1) / 2) : 0;
+    const uint64_t sj = row_bound(n, P, uint64_t(j) + 1) - row_bound(n, P, j);
+    return si * sj;
+  }
+  struct Ctx {
+    uint64_t ri, rj, sj;
+    bool tri;
+  };
+  __host__ __device__ __forceinline__ Ctx ctx(uint64_t k) const {
+    uint32_t i, j;
+    ij(k, i, j);
+    Ctx x;
+    x.ri = row_bound(n, P, i);
+    x.rj = row_bound(n, P, j);
+    x.sj = row_bound(n, P, uint64_t(j) + 1) - x.rj;
+    x.tri = (i == j);
+    return x;
+  }
+  __host__ __device__ __forceinline__ void map(const Ctx& x, uint64_t off, uint64_t& u,
+                                               uint64_t& v) const {
+    if (!x.tri) {
+      const uint64_t q = off / x.sj;
+      u = x.ri + q;
+      v = x.rj + (off - q * x.sj);
+      return;
+    }
+    // largest w with w(w-1)/2 <= off, from the square root, then corrected
+    uint64_t w = uint64_t((1.0 + sqrt(1.0 + 8.0 * double(off))) * 0.5);
+    if (w < 1) w = 1;
+    while (u128(w) * (w - 1) / 2 > off) --w;
+    while (u128(w + 1) * w / 2 <= off) ++w;
+    u = x.ri + w;
+    v = x.ri + (off - uint64_t(u128(w) * (w - 1) / 2));
+  }
+};
+
+// Leaf universe of tile tau: [min(tau W, U), min((tau+1) W, U)), W = ceil(U/2^d).
+__host__ __device__ __forceinline__ uint64_t tile_width(uint64_t U, int d) {
+  return uint64_t((u128(U) + ((u128(1) << d) - 1)) >> d);
+}
+// Left end of tile-tree node (level, j): min(floor(j W 2^d / 2^level), U).
+__host__ __device__ __forceinline__ uint64_t node_bound(uint64_t U, uint64_t W, int d, int level,
+                                                        u128 j) {
+  u128 x = j * u128(W);
+  if (level <= d)
+    x <<= (d - level);
+  else
+    x >>= (level - d);
+  return x < u128(U) ? uint64_t(x) : U;
+}
+
+// ---------------------------------------------------------------- block scan
+// Inclusive scan of one value per thread over the block; returns the block total.
+template <int NT, class T>
+__device__ __forceinline__ T block_inclusive_scan(T x, T& total) {
+  __shared__ T warp_tot[NT / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    T y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    T w = lane < NT / 32 ? warp_tot[lane] : T(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      T y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < NT / 32) warp_tot[lane] = w;
+  }
+  __syncthreads();
+  if (wid > 0) x += warp_tot[wid - 1];
+  total = warp_tot[NT / 32 - 1];
+  __syncthreads();
+  return x;
+}
+
+}  // namespace kg

@@ -1,0 +1,399 @@
+// G(n,m) kernels: chunk split tree (Sec. 4.1), tile tree inside the chunks
+// (the divide-and-conquer recursion of Sec. 2.2 continued below the chunk),
+// and the leaf kernel that samples each tile without replacement (Floyd),
+// sorts it in shared memory and emits (u, v) pairs with coalesced stores.
+#pragma once
+#include "kg_common.cuh"
+
+namespace kg {
+
+// ---------------------------------------------------------------- chunk tree
+// Range [a, b) of heap node h at depth `level`; false if an ancestor is a leaf.
+__device__ __forceinline__ bool chunk_range(uint32_t P, uint64_t h, int level, uint32_t& a,
+                                            uint32_t& b) {
+  a = 0;
+  b = P;
+  for (int bit = level - 1; bit >= 0; --bit) {
+    if (b - a < 2) return false;
+    const uint32_t s = a + (b - a + 1) / 2;
+    if ((h >> bit) & 1)
+      a = s;
+    else
+      b = s;
+  }
+  return true;
+}
+
+// Levels [l0, l1) of the directed chunk tree, one block per subtree rooted at
+// level l0.  Node h with range [a,b) and count mc splits at s = a + ceil((b-a)/2)
+// (l = ceil(P/2)) by X = Hyp(rows[a,b)(n-1), rows[a,s)(n-1), mc).
+__global__ void chunk_tree_band(uint64_t n, uint32_t P, uint64_t seed, uint64_t m, int l0, int l1,
+                                uint64_t* __restrict__ node_cnt, uint64_t* __restrict__ cnt,
+                                int* err) {
+  const uint64_t root = (uint64_t(1) << l0) + blockIdx.x;
+  if (l0 == 0 && threadIdx.x == 0) node_cnt[1] = m;
+  __syncthreads();
+  for (int r = 0; r < l1 - l0; ++r) {
+    const int level = l0 + r;
+    const uint64_t nodes = uint64_t(1) << r;
+    for (uint64_t j = threadIdx.x; j < nodes; j += blockDim.x) {
+      const uint64_t h = (root << r) + j;
+      uint32_t a, b;
+      if (!chunk_range(P, h, level, a, b)) continue;
+      const uint64_t mc = node_cnt[h];
+      if (b - a == 1) {
+        cnt[a] = mc;
+        continue;
+      }
+      const uint32_t s = a + (b - a + 1) / 2;
+      const uint64_t ra = row_bound(n, P, a);
+      const u128 N = u128(row_bound(n, P, b) - ra) * (n - 1);
+      const u128 NL = u128(row_bound(n, P, s) - ra) * (n - 1);
+      Stream st(seed, h, TAG_CHUNK_TREE);
+      uint64_t X = 0;
+      const int e = hypergeometric(N, NL, mc, st, X);
+      if (e) {
+        set_error(err, e);
+        X = 0;
+      }
+      node_cnt[2 * h] = X;
+      node_cnt[2 * h + 1] = mc - X;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- tile tree
+// One level of the tile trees of chunks [c_begin, c_begin + C): node (c, j) at
+// `level` with count in[c 2^level + j] splits its universe at the middle tile
+// boundary; out[2 (c 2^level + j)] gets X, out[... + 1] the rest.  One warp per
+// node: a fair-bit binomial is counted by all 32 lanes, other draws by lane 0.
+template <class Geom>
+__global__ void tile_tree_level(Geom g, uint64_t c_begin, uint64_t C, int d, int level,
+                                uint64_t seed, const uint64_t* __restrict__ in,
+                                uint64_t* __restrict__ out, int* err) {
+  const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  const unsigned lane = threadIdx.x & 31;
+  const uint64_t total = C << level;
+  for (uint64_t node = warp; node < total; node += nwarps) {
+    const uint64_t c = node >> level;
+    const uint64_t j = node & ((uint64_t(1) << level) - 1);
+    const uint64_t cc = c_begin + c;
+    const uint64_t U = g.universe(cc);
+    const uint64_t W = tile_width(U, d);
+    const uint64_t lo = node_bound(U, W, d, level, j);
+    const uint64_t hi = node_bound(U, W, d, level, u128(j) + 1);
+    const uint64_t mid = node_bound(U, W, d, level + 1, u128(2) * j + 1);
+    const uint64_t k = in[node];
+    const uint64_t sid = (g.chunk_id(cc) << 32) | ((uint64_t(1) << level) + j);
+    uint64_t X = 0;
+    HyperPlan hp;
+    int st = (k > hi - lo) ? ST_INTERNAL : hyper_plan(u128(hi - lo), u128(mid - lo), k, hp);
+    if (st == ST_OK) {
+      if (hp.kind == 0) {
+        X = hp.fixed;
+      } else if (hp.kind == 1) {
+        X = hyper_finish(hp, popcount_bits_warp(seed, sid, TAG_TILE, 0, hp.t1));
+      } else {
+        if (lane == 0) {
+          Stream s(seed, sid, TAG_TILE);
+          uint64_t r = 0;
+          st = hyper_general(hp, s, r);
+          X = st ? 0 : hyper_finish(hp, r);
+        }
+        X = __shfl_sync(0xffffffffu, X, 0);
+        st = __shfl_sync(0xffffffffu, st, 0);
+      }
+    }
+    if (lane == 0) {
+      if (st) {
+        set_error(err, st);
+        X = 0;
+      }
+      out[2 * node] = X;
+      out[2 * node + 1] = k - X;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- leaf kernel
+struct LeafSmem {
+  uint64_t keys[K_MAX];    // draws t_i in draw order
+  uint64_t sorted[K_MAX];  // the same values sorted
+  uint32_t hist[K_MAX];    // bucket counts, then bucket ends
+  uint16_t first_pos[K_MAX];
+  uint32_t bitT[K_MAX / 32], bitJ[K_MAX / 32];
+  // control for the re-split walk
+  int stack_level[LEVEL_MAX + 2];
+  uint64_t stack_j[LEVEL_MAX + 2], stack_k[LEVEL_MAX + 2];
+  int sp;
+  int leaf_level;
+  uint64_t leaf_j, leaf_k;
+  int done;
+};
+
+// Edge sink: interleaved (u, v) pairs of Id (uint32_t or uint64_t); nothing
+// is written at or beyond `cap` pairs (the device error word records it).
+template <class Id>
+struct PairSink {
+  Id* out;
+  uint64_t cap;
+  int* err;
+  __device__ __forceinline__ void write(uint64_t pos, uint64_t u, uint64_t v) const {
+    if (pos >= cap) {
+      set_error(err, ST_CAPACITY);
+      return;
+    }
+    if (sizeof(Id) == 4) {
+      uint2 w;
+      w.x = uint32_t(u);
+      w.y = uint32_t(v);
+      reinterpret_cast<uint2*>(out)[pos] = w;
+    } else {
+      ulonglong2 w;
+      w.x = u;
+      w.y = v;
+      __stcs(reinterpret_cast<ulonglong2*>(out) + pos, w);
+    }
+  }
+};
+
+// Floyd's sampler on one leaf: k distinct values of [0, L) (draw i is uniform
+// on [0, L-k+i]; a value already taken is replaced by L-k+i), sorted by a
+// bucket pass in shared memory; then offsets lo + value are mapped to (u, v)
+// and written to positions base, base+1, ... .  All threads of the block call it.
+template <class Geom, class Sink>
+__device__ void leaf_sample_emit(const Geom& g, const typename Geom::Ctx& gx, const Sink& sink,
+                                 LeafSmem& sm, uint64_t seed, uint64_t node, uint64_t lo,
+                                 uint64_t L, uint32_t k, uint64_t base, int* err) {
+  const int tid = threadIdx.x;
+  const uint64_t Lk = L - k;
+  // 1. draws: thread handles pairs (i, i+1) that share one Philox block
+  for (uint32_t i = 2 * tid; i < k; i += 2 * LEAF_THREADS) {
+    uint32_t w[4];
+    philox10(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, uint32_t(seed),
+             uint32_t(seed >> 32), w);
+    const uint64_t x0 = (uint64_t(w[0]) << 32) | w[1];
+    sm.keys[i] = lemire_draw(x0, Lk + i + 1, seed, node, i);
+    if (i + 1 < k) {
+      const uint64_t x1 = (uint64_t(w[2]) << 32) | w[3];
+      sm.keys[i + 1] = lemire_draw(x1, Lk + i + 2, seed, node, i + 1);
+    }
+  }
+  // 2. bucket sort by the top bits: nb buckets (power of two >= k)
+  uint32_t nb = 64;
+  while (nb < k) nb <<= 1;
+  const int lognb = __ffs(nb) - 1;
+  const int bl = (L > 1) ? 64 - __clzll((long long)(L - 1)) : 0;  // bits of L-1
+  const int shift = bl > lognb ? bl - lognb : 0;
+  for (uint32_t b = tid; b < nb; b += LEAF_THREADS) sm.hist[b] = 0;
+  __syncthreads();
+  for (uint32_t i = tid; i < k; i += LEAF_THREADS) atomicAdd(&sm.hist[sm.keys[i] >> shift], 1u);
+  __syncthreads();
+  {
+    // exclusive scan of hist[0..nb): each thread owns nb/LEAF_THREADS (or 1) entries
+    const uint32_t per = (nb + LEAF_THREADS - 1) / LEAF_THREADS;
+    const uint32_t b0 = tid * per;
+    uint32_t s = 0;
+    for (uint32_t q = 0; q < per; ++q)
+      if (b0 + q < nb) s += sm.hist[b0 + q];
+    uint32_t tot;
+    uint32_t run = block_inclusive_scan<LEAF_THREADS>(s, tot) - s;
+    for (uint32_t q = 0; q < per; ++q)
+      if (b0 + q < nb) {
+        const uint32_t c = sm.hist[b0 + q];
+        sm.hist[b0 + q] = run;
+        run += c;
+      }
+  }
+  __syncthreads();
+  for (uint32_t i = tid; i < k; i += LEAF_THREADS) {
+    const uint64_t x = sm.keys[i];
+    const uint32_t pos = atomicAdd(&sm.hist[x >> shift], 1u);
+    sm.sorted[pos] = x;
+  }
+  __syncthreads();
+  // hist[b] is now the end of bucket b; sort inside each bucket
+  for (uint32_t b = tid; b < nb; b += LEAF_THREADS) {
+    const uint32_t s0 = b ? sm.hist[b - 1] : 0, s1 = sm.hist[b];
+    for (uint32_t x = s0 + 1; x < s1; ++x) {
+      const uint64_t key = sm.sorted[x];
+      uint32_t y = x;
+      while (y > s0 && sm.sorted[y - 1] > key) {
+        sm.sorted[y] = sm.sorted[y - 1];
+        --y;
+      }
+      sm.sorted[y] = key;
+    }
+  }
+  __syncthreads();
+  // 3. all draws distinct  <=>  Floyd never replaced a value: S = {t_i}
+  int dup = 0;
+  for (uint32_t r = tid + 1; r < k; r += LEAF_THREADS) dup |= (sm.sorted[r] == sm.sorted[r - 1]);
+  const uint64_t* res = sm.sorted;
+  if (__syncthreads_or(dup)) {
+    // Sequential resolution in draw order.  A value v < L-k can only be taken
+    // by an earlier draw of v itself (first occurrence wins); the values
+    // L-k .. L-1 are tracked in a bitmap because replacements land there.
+    for (uint32_t i = tid; i < k; i += LEAF_THREADS) {
+      const uint64_t v = sm.keys[i];
+      uint32_t a = 0, b = k;  // lower_bound in sorted
+      while (a < b) {
+        const uint32_t mid = (a + b) >> 1;
+        if (sm.sorted[mid] < v)
+          a = mid + 1;
+        else
+          b = mid;
+      }
+      sm.first_pos[i] = uint16_t(a);
+    }
+    for (uint32_t w = tid; w < K_MAX / 32; w += LEAF_THREADS) sm.bitT[w] = sm.bitJ[w] = 0;
+    __syncthreads();
+    if (tid == 0) {
+      for (uint32_t i = 0; i < k; ++i) {
+        const uint64_t v = sm.keys[i];
+        if (v < Lk) {
+          const uint32_t fp = sm.first_pos[i];
+          if (sm.bitT[fp >> 5] & (1u << (fp & 31)))
+            sm.bitJ[i >> 5] |= 1u << (i & 31);
+          else
+            sm.bitT[fp >> 5] |= 1u << (fp & 31);
+        } else {
+          const uint32_t bj = uint32_t(v - Lk);
+          if (sm.bitJ[bj >> 5] & (1u << (bj & 31)))
+            sm.bitJ[i >> 5] |= 1u << (i & 31);
+          else
+            sm.bitJ[bj >> 5] |= 1u << (bj & 31);
+        }
+      }
+      // the taken set in increasing order, written over keys[]
+      uint32_t o = 0;
+      for (uint32_t r = 0; r < k; ++r) {
+        const uint64_t v = sm.sorted[r];
+        if (v >= Lk) break;
+        if ((r == 0 || sm.sorted[r - 1] != v) && (sm.bitT[r >> 5] & (1u << (r & 31))))
+          sm.keys[o++] = v;
+      }
+      for (uint32_t bj = 0; bj < k; ++bj)
+        if (sm.bitJ[bj >> 5] & (1u << (bj & 31))) sm.keys[o++] = Lk + bj;
+      if (o != k) set_error(err, ST_INTERNAL);
+    }
+    __syncthreads();
+    res = sm.keys;
+  }
+  // 4. emit: consecutive ranks to consecutive threads (coalesced stores)
+  for (uint32_t r = tid; r < k; r += LEAF_THREADS) {
+    uint64_t u, v;
+    g.map(gx, lo + res[r], u, v);
+    sink.write(base + r, u, v);
+  }
+  __syncthreads();
+}
+
+// One block per tile of chunks [c_begin, c_begin + C) with 2^d tiles each.
+// tile_cnt / tile_off are indexed by the local tile id c 2^d + tau; a leaf with
+// more than k_max samples is split further (levels below d) by the same rule.
+template <class Geom, class Sink>
+__global__ void __launch_bounds__(LEAF_THREADS)
+    leaf_kernel(Geom g, Sink sink, uint64_t c_begin, int d, uint32_t k_max, uint64_t seed,
+                const uint64_t* __restrict__ tile_cnt, const uint64_t* __restrict__ tile_off,
+                uint64_t ntiles, int* err) {
+  __shared__ LeafSmem sm;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t k = tile_cnt[t];
+    if (k == 0) continue;
+    const uint64_t c = c_begin + (t >> d);
+    const uint64_t tau = t & ((uint64_t(1) << d) - 1);
+    const uint64_t U = g.universe(c);
+    const uint64_t W = tile_width(U, d);
+    const uint64_t cid = g.chunk_id(c);
+    const typename Geom::Ctx gx = g.ctx(c);
+    uint64_t base = tile_off[t];
+    if (k <= k_max) {
+      const uint64_t lo = node_bound(U, W, d, d, tau);
+      const uint64_t hi = node_bound(U, W, d, d, u128(tau) + 1);
+      if (k > hi - lo) {
+        if (threadIdx.x == 0) set_error(err, ST_INTERNAL);
+        continue;
+      }
+      leaf_sample_emit(g, gx, sink, sm, seed, (cid << 32) | ((uint64_t(1) << d) + tau), lo,
+                       hi - lo, uint32_t(k), base, err);
+      continue;
+    }
+    // re-split walk, left to right, driven by thread 0
+    if (threadIdx.x == 0) {
+      sm.sp = 0;
+      sm.stack_level[0] = d;
+      sm.stack_j[0] = tau;
+      sm.stack_k[0] = k;
+      sm.sp = 1;
+    }
+    for (;;) {
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        sm.done = 1;
+        while (sm.sp > 0) {
+          --sm.sp;
+          int lv = sm.stack_level[sm.sp];
+          uint64_t j = sm.stack_j[sm.sp], kk = sm.stack_k[sm.sp];
+          bool bad = false;
+          for (;;) {
+            const uint64_t lo = node_bound(U, W, d, lv, j);
+            const uint64_t hi = node_bound(U, W, d, lv, u128(j) + 1);
+            if (kk > hi - lo) {
+              set_error(err, ST_INTERNAL);
+              bad = true;
+              break;
+            }
+            if (kk <= k_max || hi - lo < 2) break;
+            if (lv + 1 > LEVEL_MAX) {
+              set_error(err, ST_INTERNAL);
+              bad = true;
+              break;
+            }
+            const uint64_t mid = node_bound(U, W, d, lv + 1, u128(2) * j + 1);
+            Stream s(seed, (cid << 32) | ((uint64_t(1) << lv) + j), TAG_TILE);
+            uint64_t X = 0;
+            const int e = hypergeometric(u128(hi - lo), u128(mid - lo), kk, s, X);
+            if (e) {
+              set_error(err, e);
+              bad = true;
+              break;
+            }
+            sm.stack_level[sm.sp] = lv + 1;
+            sm.stack_j[sm.sp] = 2 * j + 1;
+            sm.stack_k[sm.sp] = kk - X;
+            ++sm.sp;
+            ++lv;
+            j = 2 * j;
+            kk = X;
+          }
+          if (bad) {
+            sm.sp = 0;
+            break;
+          }
+          if (kk > 0) {
+            sm.leaf_level = lv;
+            sm.leaf_j = j;
+            sm.leaf_k = kk;
+            sm.done = 0;
+            break;
+          }
+        }
+      }
+      __syncthreads();
+      if (sm.done) break;
+      const int lv = sm.leaf_level;
+      const uint64_t j = sm.leaf_j;
+      const uint32_t kk = uint32_t(sm.leaf_k);
+      const uint64_t lo = node_bound(U, W, d, lv, j);
+      const uint64_t hi = node_bound(U, W, d, lv, u128(j) + 1);
+      leaf_sample_emit(g, gx, sink, sm, seed, (cid << 32) | ((uint64_t(1) << lv) + j), lo, hi - lo,
+                       kk, base, err);
+      base += kk;
+    }
+  }
+}
+
+}  // namespace kg
