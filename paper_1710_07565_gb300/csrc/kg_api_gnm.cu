@@ -5,7 +5,7 @@
 
 #include "../../include/kg.h"
 #include "kg_digest.cuh"
-#include "kg_gnm.cuh"
+#include "kg_leaf.cuh"
 #include "kg_internal.h"
 #include "kg_prof.h"
 
@@ -58,11 +58,36 @@ static unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
 static int launch_ok() { return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA; }
 
 // Tile trees + scan + leaves for chunks [c_begin, c_begin + C) of a geometry.
-// level0: the chunks' counts (device).  Pairs go to d_out[0 ..).
+// level0: the chunks' counts (device).  Pairs go to d_out[0 ..).  With digest
+// pointers the leaf kernel also produces the per-chunk digest and out-degree
+// histogram (directed geometry only).
+template <class Geom, class Sink, bool DIGEST>
+static int launch_leaf(const Geom& g, const Sink& sink, uint64_t c_begin, int d, uint32_t k_max,
+                       uint64_t seed, const uint64_t* tile_cnt, const uint64_t* tile_off,
+                       uint64_t T, int* err, DigestOut dig, Workspace& ws, cudaStream_t s) {
+  unsigned long long* big = ws.alloc<unsigned long long>(T);
+  unsigned long long* nbig = ws.alloc<unsigned long long>(1);
+  if (!ws.ok()) return ST_CUDA;
+  if (cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), s) != cudaSuccess) return ST_CUDA;
+  const unsigned grid = unsigned(T < 0x7fffffffull ? T : 0x7fffffffull);
+  {
+    ProfScope ps(PROF_LEAF, s);
+    leaf_fast_kernel<Geom, Sink, DIGEST><<<grid, FAST_THREADS, 0, s>>>(
+        g, sink, c_begin, d, k_max, seed, round_keys(seed), tile_cnt, tile_off, T, err, dig, big,
+        nbig);
+    if (launch_ok()) return ST_CUDA;
+  }
+  ProfScope ps(PROF_OTHER, s);
+  leaf_resplit_kernel<Geom, Sink, DIGEST><<<152, LEAF_THREADS, 0, s>>>(
+      g, sink, c_begin, d, k_max, seed, tile_cnt, tile_off, err, dig, big, nbig);
+  return launch_ok();
+}
+
 template <class Geom>
 int run_chunks(const Geom& g, uint64_t c_begin, uint64_t C, const uint64_t* level0, int d,
                uint32_t k_max, uint64_t seed, int id_bytes, void* d_out, uint64_t cap,
-               Workspace& ws, cudaStream_t s, int* err) {
+               Workspace& ws, cudaStream_t s, int* err, uint64_t* digest = nullptr,
+               uint64_t* hist = nullptr) {
   const uint64_t T = C << d;
   const uint64_t* in = level0;
   if (d > 0) {
@@ -73,7 +98,7 @@ int run_chunks(const Geom& g, uint64_t c_begin, uint64_t C, const uint64_t* leve
       uint64_t* out = (level & 1) ? B : A;
       const uint64_t nodes = C << level;
       ProfScope ps(PROF_TILE_TREE, s);
-      tile_tree_level<Geom><<<grid_for(nodes, 8, 152 * 128), 256, 0, s>>>(
+      tile_tree_level<Geom><<<grid_for(nodes, 256, 152 * 16), 256, 0, s>>>(
           g, c_begin, C, d, level, seed, in, out, err);
       if (launch_ok()) return ST_CUDA;
       in = out;
@@ -83,17 +108,35 @@ int run_chunks(const Geom& g, uint64_t c_begin, uint64_t C, const uint64_t* leve
   if (!ws.ok()) return ST_CUDA;
   int st = scan_exclusive_u64(in, tile_off, T, ws, s);
   if (st) return st;
-  const unsigned grid = unsigned(T < 0x7fffffffull ? T : 0x7fffffffull);
-  ProfScope ps(PROF_LEAF, s);
+  const bool want = digest || hist;
+  DigestOut dig{nullptr, nullptr, nullptr};
+  if (want) {
+    dig.digest = reinterpret_cast<unsigned long long*>(digest ? digest : ws.alloc<uint64_t>(C));
+    dig.hist = reinterpret_cast<unsigned long long*>(hist ? hist : ws.alloc<uint64_t>(C * 65));
+    dig.rec = ws.alloc<TileRec>(T);
+    if (!ws.ok()) return ST_CUDA;
+    if (cudaMemsetAsync(dig.digest, 0, C * sizeof(uint64_t), s) != cudaSuccess ||
+        cudaMemsetAsync(dig.hist, 0, C * 65 * sizeof(uint64_t), s) != cudaSuccess ||
+        cudaMemsetAsync(dig.rec, 0, T * sizeof(TileRec), s) != cudaSuccess)
+      return ST_CUDA;
+  }
   if (id_bytes == 4) {
     PairSink<uint32_t> sink{static_cast<uint32_t*>(d_out), cap, err};
-    leaf_kernel<Geom, PairSink<uint32_t>><<<grid, LEAF_THREADS, 0, s>>>(
-        g, sink, c_begin, d, k_max, seed, in, tile_off, T, err);
+    st = want ? launch_leaf<Geom, PairSink<uint32_t>, true>(g, sink, c_begin, d, k_max, seed, in,
+                                                             tile_off, T, err, dig, ws, s)
+              : launch_leaf<Geom, PairSink<uint32_t>, false>(g, sink, c_begin, d, k_max, seed, in,
+                                                              tile_off, T, err, dig, ws, s);
   } else {
     PairSink<uint64_t> sink{static_cast<uint64_t*>(d_out), cap, err};
-    leaf_kernel<Geom, PairSink<uint64_t>><<<grid, LEAF_THREADS, 0, s>>>(
-        g, sink, c_begin, d, k_max, seed, in, tile_off, T, err);
+    st = want ? launch_leaf<Geom, PairSink<uint64_t>, true>(g, sink, c_begin, d, k_max, seed, in,
+                                                             tile_off, T, err, dig, ws, s)
+              : launch_leaf<Geom, PairSink<uint64_t>, false>(g, sink, c_begin, d, k_max, seed, in,
+                                                              tile_off, T, err, dig, ws, s);
   }
+  if (st || !want) return st;
+  ProfScope ps(PROF_DIGEST, s);
+  chunk_run_merge<Geom><<<grid_for(C, 128, 152 * 8), 128, 0, s>>>(g, c_begin, C, d, dig.rec,
+                                                                   dig.hist);
   return launch_ok();
 }
 
@@ -133,6 +176,7 @@ static DirGeom dir_geom(uint64_t n, uint32_t P) {
   g.n = n;
   g.P = P;
   g.div = make_div(n > 1 ? n - 1 : 1);
+  g.rb = RowBounds::make(n, P);
   return g;
 }
 
@@ -144,8 +188,8 @@ static int run_chunk_tree(const DirParams& dp, uint64_t seed, uint64_t* cnt, Wor
   for (int l0 = 0; l0 <= dp.D; l0 += 8) {
     const int l1 = (l0 + 8 < dp.D + 1) ? l0 + 8 : dp.D + 1;
     ProfScope ps(PROF_CHUNK_TREE, s);
-    chunk_tree_band<<<unsigned(1) << l0, 256, 0, s>>>(dp.n, dp.P, seed, dp.m, l0, l1, node_cnt, cnt,
-                                                       err);
+    chunk_tree_band<<<unsigned(1) << l0, 256, 0, s>>>(RowBounds::make(dp.n, dp.P), seed, dp.m, l0,
+                                                       l1, node_cnt, cnt, err);
     if (launch_ok()) return ST_CUDA;
   }
   return ST_OK;
@@ -238,16 +282,7 @@ kg_status kg_gnm_directed_range(uint64_t n, uint64_t m, uint64_t seed, uint32_t 
   Workspace ws(s);
   const DirGeom g = dir_geom(n, chunks);
   st = run_chunks(g, c_begin, C, d_counts + c_begin, dp.d, K_MAX, seed, id_bytes, d_out, cap_edges,
-                  ws, s, err);
-  if (st) return kg_status(st);
-  if (d_chunk_digest || d_chunk_hist) {
-    uint64_t* chunk_off = ws.alloc<uint64_t>(C + 1);
-    if (!ws.ok()) return KG_ERR_CUDA;
-    st = scan_exclusive_u64(d_counts + c_begin, chunk_off, C, ws, s);
-    if (st) return kg_status(st);
-    st = chunk_digest(g, c_begin, C, chunk_off, id_bytes, d_out, cap_edges, d_chunk_digest,
-                      d_chunk_hist, s);
-  }
+                  ws, s, err, d_chunk_digest, d_chunk_hist);
   return kg_status(st);
 }
 

@@ -22,21 +22,43 @@ __host__ __device__ __forceinline__ uint64_t row_bound(uint64_t n, uint32_t P, u
   return uint64_t((u128(c) * n) / P);
 }
 
+// r_c without 128-bit division: with n = qP + r, floor(cn/P) = cq + floor(cr/P)
+// and cr < 2^48 for c <= P <= 2^24, divided through an invariant multiplier.
+struct RowBounds {
+  uint64_t n, q, r;
+  uint32_t P;
+  DivU64 divP;
+  static RowBounds make(uint64_t n_, uint32_t P_) {
+    RowBounds b;
+    b.n = n_;
+    b.P = P_;
+    b.q = n_ / P_;
+    b.r = n_ % P_;
+    b.divP = make_div(P_);
+    return b;
+  }
+  __host__ __device__ __forceinline__ uint64_t operator()(uint64_t c) const {
+    return c * q + div_q(divP, c * r);
+  }
+};
+
 // Directed chunks (Sec. 4.1): chunk c = rows [r_c, r_{c+1}) x all n-1 columns
 // other than the row itself; offsets are row-major, the diagonal skipped.
 struct DirGeom {
   uint64_t n;
   uint32_t P;
   DivU64 div;  // division by n-1
+  RowBounds rb;
 
   __host__ __device__ __forceinline__ uint64_t chunk_id(uint64_t c) const { return c; }
+  __host__ __device__ __forceinline__ uint64_t rows(uint64_t c) const { return rb(c + 1) - rb(c); }
   __host__ __device__ __forceinline__ uint64_t universe(uint64_t c) const {
-    return (row_bound(n, P, c + 1) - row_bound(n, P, c)) * (n - 1);
+    return rows(c) * (n - 1);
   }
   struct Ctx {
     uint64_t r0;
   };
-  __host__ __device__ __forceinline__ Ctx ctx(uint64_t c) const { return Ctx{row_bound(n, P, c)}; }
+  __host__ __device__ __forceinline__ Ctx ctx(uint64_t c) const { return Ctx{rb(c)}; }
   __host__ __device__ __forceinline__ void map(const Ctx& x, uint64_t off, uint64_t& u,
                                                uint64_t& v) const {
     const uint64_t q = div_q(div, off);
@@ -53,6 +75,7 @@ struct DirGeom {
 struct UndGeom {
   uint64_t n;
   uint32_t P;
+  RowBounds rb;
 
   __host__ __device__ __forceinline__ static void ij(uint64_t k, uint32_t& i, uint32_t& j) {
     uint64_t r = uint64_t(sqrt(8.0 * double(k) + 1.0) - 1.0) / 2;
@@ -69,9 +92,9 @@ struct UndGeom {
   __host__ __device__ __forceinline__ uint64_t universe(uint64_t k) const {
     uint32_t i, j;
     ij(k, i, j);
-    const uint64_t si = row_bound(n, P, uint64_t(i) + 1) - row_bound(n, P, i);
+    const uint64_t si = rb(uint64_t(i) + 1) - rb(i);
     if (i == j) return si ? uint64_t(u128(si) * (si - 1) / 2) : 0;
-    const uint64_t sj = row_bound(n, P, uint64_t(j) + 1) - row_bound(n, P, j);
+    const uint64_t sj = rb(uint64_t(j) + 1) - rb(j);
     return si * sj;
   }
   struct Ctx {
@@ -82,9 +105,9 @@ struct UndGeom {
     uint32_t i, j;
     ij(k, i, j);
     Ctx x;
-    x.ri = row_bound(n, P, i);
-    x.rj = row_bound(n, P, j);
-    x.sj = row_bound(n, P, uint64_t(j) + 1) - x.rj;
+    x.ri = rb(i);
+    x.rj = rb(j);
+    x.sj = rb(uint64_t(j) + 1) - x.rj;
     x.tri = (i == j);
     return x;
   }

@@ -27,9 +27,11 @@ __device__ __forceinline__ bool chunk_range(uint32_t P, uint64_t h, int level, u
 // Levels [l0, l1) of the directed chunk tree, one block per subtree rooted at
 // level l0.  Node h with range [a,b) and count mc splits at s = a + ceil((b-a)/2)
 // (l = ceil(P/2)) by X = Hyp(rows[a,b)(n-1), rows[a,s)(n-1), mc).
-__global__ void chunk_tree_band(uint64_t n, uint32_t P, uint64_t seed, uint64_t m, int l0, int l1,
+__global__ void chunk_tree_band(RowBounds rb, uint64_t seed, uint64_t m, int l0, int l1,
                                 uint64_t* __restrict__ node_cnt, uint64_t* __restrict__ cnt,
                                 int* err) {
+  const uint64_t n = rb.n;
+  const uint32_t P = rb.P;
   const uint64_t root = (uint64_t(1) << l0) + blockIdx.x;
   if (l0 == 0 && threadIdx.x == 0) node_cnt[1] = m;
   __syncthreads();
@@ -46,9 +48,9 @@ __global__ void chunk_tree_band(uint64_t n, uint32_t P, uint64_t seed, uint64_t 
         continue;
       }
       const uint32_t s = a + (b - a + 1) / 2;
-      const uint64_t ra = row_bound(n, P, a);
-      const u128 N = u128(row_bound(n, P, b) - ra) * (n - 1);
-      const u128 NL = u128(row_bound(n, P, s) - ra) * (n - 1);
+      const uint64_t ra = rb(a);
+      const u128 N = u128(rb(b) - ra) * (n - 1);
+      const u128 NL = u128(rb(s) - ra) * (n - 1);
       Stream st(seed, h, TAG_CHUNK_TREE);
       uint64_t X = 0;
       const int e = hypergeometric(N, NL, mc, st, X);
@@ -66,47 +68,58 @@ __global__ void chunk_tree_band(uint64_t n, uint32_t P, uint64_t seed, uint64_t 
 // ---------------------------------------------------------------- tile tree
 // One level of the tile trees of chunks [c_begin, c_begin + C): node (c, j) at
 // `level` with count in[c 2^level + j] splits its universe at the middle tile
-// boundary; out[2 (c 2^level + j)] gets X, out[... + 1] the rest.  One warp per
-// node: a fair-bit binomial is counted by all 32 lanes, other draws by lane 0.
+// boundary; out[2 (c 2^level + j)] gets X, out[... + 1] the rest.
+// Lane i of a warp owns node 32w + i: FP64 draws run on all lanes at once;
+// fair-bit binomials are then counted by the whole warp, one node at a time.
 template <class Geom>
-__global__ void tile_tree_level(Geom g, uint64_t c_begin, uint64_t C, int d, int level,
-                                uint64_t seed, const uint64_t* __restrict__ in,
-                                uint64_t* __restrict__ out, int* err) {
-  const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+__global__ void __launch_bounds__(256)
+    tile_tree_level(Geom g, uint64_t c_begin, uint64_t C, int d, int level, uint64_t seed,
+                    const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int* err) {
   const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
   const unsigned lane = threadIdx.x & 31;
   const uint64_t total = C << level;
-  for (uint64_t node = warp; node < total; node += nwarps) {
-    const uint64_t c = node >> level;
-    const uint64_t j = node & ((uint64_t(1) << level) - 1);
-    const uint64_t cc = c_begin + c;
-    const uint64_t U = g.universe(cc);
-    const uint64_t W = tile_width(U, d);
-    const uint64_t lo = node_bound(U, W, d, level, j);
-    const uint64_t hi = node_bound(U, W, d, level, u128(j) + 1);
-    const uint64_t mid = node_bound(U, W, d, level + 1, u128(2) * j + 1);
-    const uint64_t k = in[node];
-    const uint64_t sid = (g.chunk_id(cc) << 32) | ((uint64_t(1) << level) + j);
-    uint64_t X = 0;
+  for (uint64_t base = ((uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5) * 32; base < total;
+       base += nwarps * 32) {
+    const uint64_t node = base + lane;
+    const bool live = node < total;
+    uint64_t X = 0, k = 0, sid = 0;
+    int st = ST_OK;
     HyperPlan hp;
-    int st = (k > hi - lo) ? ST_INTERNAL : hyper_plan(u128(hi - lo), u128(mid - lo), k, hp);
-    if (st == ST_OK) {
-      if (hp.kind == 0) {
-        X = hp.fixed;
-      } else if (hp.kind == 1) {
-        X = hyper_finish(hp, popcount_bits_warp(seed, sid, TAG_TILE, 0, hp.t1));
-      } else {
-        if (lane == 0) {
+    hp.kind = 0;
+    hp.fixed = 0;
+    if (live) {
+      const uint64_t c = node >> level;
+      const uint64_t j = node & ((uint64_t(1) << level) - 1);
+      const uint64_t cc = c_begin + c;
+      const uint64_t U = g.universe(cc);
+      const uint64_t W = tile_width(U, d);
+      const uint64_t lo = node_bound(U, W, d, level, j);
+      const uint64_t hi = node_bound(U, W, d, level, u128(j) + 1);
+      const uint64_t mid = node_bound(U, W, d, level + 1, u128(2) * j + 1);
+      k = in[node];
+      sid = (g.chunk_id(cc) << 32) | ((uint64_t(1) << level) + j);
+      st = (k > hi - lo) ? ST_INTERNAL : hyper_plan(u128(hi - lo), u128(mid - lo), k, hp);
+      if (st == ST_OK) {
+        if (hp.kind == 0) {
+          X = hp.fixed;
+        } else if (hp.kind == 2) {
           Stream s(seed, sid, TAG_TILE);
           uint64_t r = 0;
           st = hyper_general(hp, s, r);
           X = st ? 0 : hyper_finish(hp, r);
         }
-        X = __shfl_sync(0xffffffffu, X, 0);
-        st = __shfl_sync(0xffffffffu, st, 0);
       }
     }
-    if (lane == 0) {
+    unsigned todo = __ballot_sync(0xffffffffu, live && st == ST_OK && hp.kind == 1);
+    while (todo) {
+      const int src = __ffs(todo) - 1;
+      todo &= todo - 1;
+      const uint64_t ssid = __shfl_sync(0xffffffffu, sid, src);
+      const uint64_t st1 = __shfl_sync(0xffffffffu, hp.t1, src);
+      const uint64_t r = popcount_bits_warp(seed, ssid, TAG_TILE, 0, st1);
+      if (lane == unsigned(src)) X = hyper_finish(hp, r);
+    }
+    if (live) {
       if (st) {
         set_error(err, st);
         X = 0;
@@ -157,16 +170,22 @@ struct PairSink {
       __stcs(reinterpret_cast<ulonglong2*>(out) + pos, w);
     }
   }
+  __device__ __forceinline__ uint64_t read_u(uint64_t pos) const {
+    if (pos >= cap) return ~uint64_t(0);
+    return sizeof(Id) == 4 ? uint64_t(reinterpret_cast<const uint2*>(out)[pos].x)
+                           : reinterpret_cast<const ulonglong2*>(out)[pos].x;
+  }
 };
 
 // Floyd's sampler on one leaf: k distinct values of [0, L) (draw i is uniform
 // on [0, L-k+i]; a value already taken is replaced by L-k+i), sorted by a
 // bucket pass in shared memory; then offsets lo + value are mapped to (u, v)
 // and written to positions base, base+1, ... .  All threads of the block call it.
-template <class Geom, class Sink>
-__device__ void leaf_sample_emit(const Geom& g, const typename Geom::Ctx& gx, const Sink& sink,
-                                 LeafSmem& sm, uint64_t seed, uint64_t node, uint64_t lo,
-                                 uint64_t L, uint32_t k, uint64_t base, int* err) {
+template <class Geom, class Sink, bool DIGEST>
+__device__ uint64_t* leaf_sample_emit(const Geom& g, const typename Geom::Ctx& gx,
+                                      const Sink& sink, LeafSmem& sm, uint64_t seed,
+                                      uint64_t node, uint64_t lo, uint64_t L, uint32_t k,
+                                      uint64_t base, int* err, unsigned long long& dsum) {
   const int tid = threadIdx.x;
   const uint64_t Lk = L - k;
   // 1. draws: thread handles pairs (i, i+1) that share one Philox block
@@ -231,7 +250,7 @@ __device__ void leaf_sample_emit(const Geom& g, const typename Geom::Ctx& gx, co
   // 3. all draws distinct  <=>  Floyd never replaced a value: S = {t_i}
   int dup = 0;
   for (uint32_t r = tid + 1; r < k; r += LEAF_THREADS) dup |= (sm.sorted[r] == sm.sorted[r - 1]);
-  const uint64_t* res = sm.sorted;
+  uint64_t* res = sm.sorted;
   if (__syncthreads_or(dup)) {
     // Sequential resolution in draw order.  A value v < L-k can only be taken
     // by an earlier draw of v itself (first occurrence wins); the values
@@ -282,27 +301,189 @@ __device__ void leaf_sample_emit(const Geom& g, const typename Geom::Ctx& gx, co
     __syncthreads();
     res = sm.keys;
   }
-  // 4. emit: consecutive ranks to consecutive threads (coalesced stores)
+  // 4. emit: consecutive ranks to consecutive threads (coalesced stores);
+  // with DIGEST the row u replaces the offset in place for the run analysis
   for (uint32_t r = tid; r < k; r += LEAF_THREADS) {
     uint64_t u, v;
     g.map(gx, lo + res[r], u, v);
     sink.write(base + r, u, v);
+    if (DIGEST) {
+      dsum += edge_hash(u, v);
+      res[r] = u;
+    }
   }
+  __syncthreads();
+  return res;
+}
+
+// ---------------------------------------------------------------- fused digest
+// Per tile: the digest sum, the out-degree histogram of runs of equal u that
+// lie strictly inside the tile, and a record of the first / last run, which
+// may continue in the neighbouring tiles (merged per chunk afterwards).
+struct TileRec {
+  uint64_t first_u, last_u;
+  uint32_t first_len, last_len, nruns, pad;
+};
+
+struct DigestOut {
+  unsigned long long* digest;  // per chunk of the range
+  unsigned long long* hist;    // per chunk x 65
+  TileRec* rec;                // per tile of the range
+};
+
+struct NoDigest {};
+
+template <class Acc>
+__device__ __forceinline__ void tile_runs(const Acc& u_at, uint32_t k, uint32_t& c1, uint32_t& nr,
+                                          unsigned* bh, uint64_t& fu, uint32_t& fl, uint64_t& lu,
+                                          uint32_t& ll) {
+  for (uint32_t r = threadIdx.x; r < k; r += LEAF_THREADS) {
+    const uint64_t u = u_at(r);
+    if (r > 0 && u_at(r - 1) == u) continue;
+    uint32_t len = 1;
+    while (r + len < k && u_at(r + len) == u) ++len;
+    ++nr;
+    const bool first = (r == 0), last = (r + len == k);
+    if (first) {
+      fu = u;
+      fl = len;
+    }
+    if (last) {
+      lu = u;
+      ll = len;
+    }
+    if (!first && !last) {
+      if (len == 1)
+        ++c1;
+      else
+        atomicAdd(&bh[len < 64 ? len : 64], 1u);
+    }
+  }
+}
+
+// Block-wide totals of one tile, added to its chunk; thread 0 writes the record.
+__device__ __forceinline__ void tile_digest_finish(
+    const DigestOut& dig, uint64_t t, uint64_t c_local, unsigned long long dsum, uint32_t c1,
+    uint32_t nr, uint64_t fu, uint32_t fl, uint64_t lu, uint32_t ll, unsigned* bh,
+    unsigned long long* red_d, unsigned* red_c1, unsigned* red_nr, uint64_t& s_fu, uint32_t& s_fl,
+    uint64_t& s_lu, uint32_t& s_ll) {
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+    nr += __shfl_xor_sync(0xffffffffu, nr, o);
+  }
+  if (lane == 0) {
+    red_d[wid] = dsum;
+    red_c1[wid] = c1;
+    red_nr[wid] = nr;
+  }
+  if (fl) {  // the thread that saw rank 0
+    s_fu = fu;
+    s_fl = fl;
+  }
+  if (ll) {  // the thread that saw the last rank
+    s_lu = lu;
+    s_ll = ll;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long D = 0;
+    unsigned C1 = 0, NR = 0;
+    for (int w = 0; w < LEAF_THREADS / 32; ++w) {
+      D += red_d[w];
+      C1 += red_c1[w];
+      NR += red_nr[w];
+    }
+    atomicAdd(&dig.digest[c_local], D);
+    if (C1) atomicAdd(&dig.hist[c_local * 65 + 1], (unsigned long long)C1);
+    TileRec rc;
+    rc.first_u = s_fu;
+    rc.first_len = s_fl;
+    rc.last_u = s_lu;
+    rc.last_len = s_ll;
+    rc.nruns = NR;
+    rc.pad = 0;
+    dig.rec[t] = rc;
+  }
+  for (int b = threadIdx.x; b < 65; b += LEAF_THREADS)
+    if (bh[b]) atomicAdd(&dig.hist[c_local * 65 + b], (unsigned long long)bh[b]);
   __syncthreads();
 }
 
-// One block per tile of chunks [c_begin, c_begin + C) with 2^d tiles each.
-// tile_cnt / tile_off are indexed by the local tile id c 2^d + tau; a leaf with
-// more than k_max samples is split further (levels below d) by the same rule.
-template <class Geom, class Sink>
+// Per chunk: merge the first / last runs of consecutive tiles into whole rows,
+// histogram them, and count the rows without out-edges into bin 0.
+template <class Geom>
+__global__ void chunk_run_merge(Geom g, uint64_t c_begin, uint64_t C, int d,
+                                const TileRec* __restrict__ rec,
+                                unsigned long long* __restrict__ hist) {
+  for (uint64_t c = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < C;
+       c += uint64_t(gridDim.x) * blockDim.x) {
+    unsigned long long* h = hist + c * 65;
+    bool open = false;
+    uint64_t ou = 0, ol = 0, distinct = 0;
+    const uint64_t t0 = c << d, t1 = (c + 1) << d;
+    for (uint64_t t = t0; t < t1; ++t) {
+      const TileRec r = rec[t];
+      if (r.nruns == 0) continue;
+      distinct += r.nruns;
+      if (open && r.first_u == ou) {
+        --distinct;
+        if (r.nruns == 1) {
+          ol += r.first_len;
+          continue;
+        }
+        ol += r.first_len;
+        atomicAdd(&h[ol < 64 ? ol : 64], 1ull);
+        ou = r.last_u;
+        ol = r.last_len;
+        continue;
+      }
+      if (open) atomicAdd(&h[ol < 64 ? ol : 64], 1ull);
+      if (r.nruns == 1) {
+        open = true;
+        ou = r.first_u;
+        ol = r.first_len;
+      } else {
+        atomicAdd(&h[r.first_len < 64 ? r.first_len : 64], 1ull);
+        open = true;
+        ou = r.last_u;
+        ol = r.last_len;
+      }
+    }
+    if (open) atomicAdd(&h[ol < 64 ? ol : 64], 1ull);
+    const uint64_t rows = g.rows(c_begin + c);
+    atomicAdd(&h[0], (unsigned long long)(rows - distinct));
+  }
+}
+
+// Tiles with more than k_max samples: split further (levels below d) by the
+// same hypergeometric rule, left to right, until every leaf holds at most
+// k_max samples; the leaves are emitted in order from the tile's offset.
+template <class Geom, class Sink, bool DIGEST>
 __global__ void __launch_bounds__(LEAF_THREADS)
-    leaf_kernel(Geom g, Sink sink, uint64_t c_begin, int d, uint32_t k_max, uint64_t seed,
-                const uint64_t* __restrict__ tile_cnt, const uint64_t* __restrict__ tile_off,
-                uint64_t ntiles, int* err) {
+    leaf_resplit_kernel(Geom g, Sink sink, uint64_t c_begin, int d, uint32_t k_max, uint64_t seed,
+                        const uint64_t* __restrict__ tile_cnt, const uint64_t* __restrict__ tile_off,
+                        int* err, DigestOut dig, const unsigned long long* __restrict__ big,
+                        const unsigned long long* __restrict__ nbig) {
   __shared__ LeafSmem sm;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  __shared__ unsigned bh[65];
+  __shared__ unsigned long long red_d[LEAF_THREADS / 32];
+  __shared__ unsigned red_c1[LEAF_THREADS / 32], red_nr[LEAF_THREADS / 32];
+  __shared__ uint64_t s_fu, s_lu;
+  __shared__ uint32_t s_fl, s_ll;
+  const unsigned long long nb = *nbig;
+  for (unsigned long long bi = blockIdx.x; bi < nb; bi += gridDim.x) {
+    const uint64_t t = big[bi];
     const uint64_t k = tile_cnt[t];
-    if (k == 0) continue;
+    unsigned long long dsum = 0;
+    uint32_t c1 = 0, nr = 0;
+    uint64_t fu = 0, lu = 0;
+    uint32_t fl = 0, ll = 0;
+    if (DIGEST) {
+      for (int b = threadIdx.x; b < 65; b += LEAF_THREADS) bh[b] = 0;
+    }
     const uint64_t c = c_begin + (t >> d);
     const uint64_t tau = t & ((uint64_t(1) << d) - 1);
     const uint64_t U = g.universe(c);
@@ -310,20 +491,8 @@ __global__ void __launch_bounds__(LEAF_THREADS)
     const uint64_t cid = g.chunk_id(c);
     const typename Geom::Ctx gx = g.ctx(c);
     uint64_t base = tile_off[t];
-    if (k <= k_max) {
-      const uint64_t lo = node_bound(U, W, d, d, tau);
-      const uint64_t hi = node_bound(U, W, d, d, u128(tau) + 1);
-      if (k > hi - lo) {
-        if (threadIdx.x == 0) set_error(err, ST_INTERNAL);
-        continue;
-      }
-      leaf_sample_emit(g, gx, sink, sm, seed, (cid << 32) | ((uint64_t(1) << d) + tau), lo,
-                       hi - lo, uint32_t(k), base, err);
-      continue;
-    }
-    // re-split walk, left to right, driven by thread 0
+    const uint64_t base0 = base;
     if (threadIdx.x == 0) {
-      sm.sp = 0;
       sm.stack_level[0] = d;
       sm.stack_j[0] = tau;
       sm.stack_k[0] = k;
@@ -389,9 +558,18 @@ __global__ void __launch_bounds__(LEAF_THREADS)
       const uint32_t kk = uint32_t(sm.leaf_k);
       const uint64_t lo = node_bound(U, W, d, lv, j);
       const uint64_t hi = node_bound(U, W, d, lv, u128(j) + 1);
-      leaf_sample_emit(g, gx, sink, sm, seed, (cid << 32) | ((uint64_t(1) << lv) + j), lo, hi - lo,
-                       kk, base, err);
+      leaf_sample_emit<Geom, Sink, DIGEST>(g, gx, sink, sm, seed,
+                                           (cid << 32) | ((uint64_t(1) << lv) + j), lo, hi - lo,
+                                           kk, base, err, dsum);
       base += kk;
+    }
+    if (DIGEST) {
+      // the tile's rows are read back from the output just written
+      __syncthreads();
+      auto at = [&sink, base0](uint32_t r) { return sink.read_u(base0 + r); };
+      tile_runs(at, uint32_t(base - base0), c1, nr, bh, fu, fl, lu, ll);
+      tile_digest_finish(dig, t, t >> d, dsum, c1, nr, fu, fl, lu, ll, bh, red_d, red_c1, red_nr,
+                         s_fu, s_fl, s_lu, s_ll);
     }
   }
 }
