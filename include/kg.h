@@ -129,6 +129,41 @@ kg_status kg_gnp_ex(int undirected, uint64_t n, double p, uint64_t seed, uint32_
                     uint32_t k_leaf, int id_bytes, void* d_out, uint64_t cap_edges,
                     uint64_t* d_count, void* stream);
 
+/*
+ * kg_gnm_directed_noalloc -- directed G(n,m) that allocates no memory.
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not let a library allocate device memory: a framework whose
+ * caching allocator already holds (almost) all of the GPU's memory, where a
+ * pool allocation would fail or fragment it, or an application that sets
+ * up all its memory before its steady-state loop and forbids allocation
+ * inside it, because allocation can synchronise the device and its latency
+ * has no bound.
+ *
+ * Output: the same bytes as kg_gnm_directed with the same arguments.
+ * Scratch: one array of KG_NOALLOC_SCRATCH_BYTES bytes compiled into the
+ * library as a file-scope __device__ variable; every GPU that loads the
+ * library holds it until the process exits.  Instances whose scratch would
+ * not fit are rejected with KG_ERR_RANGE before any work is enqueued (about
+ * a million tiles, i.e. m up to roughly 10^9 with the default leaf size).
+ * The call itself makes no cudaMalloc / cudaFree / pool allocation.
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it; make that
+ * first call before any stream capture.
+ * Sharing: all calls use the same array, which keeps whatever the last call
+ * left in it; each call clears what must start at zero.  Calls whose work
+ * overlaps on the GPU (other streams, or a second call before the first one
+ * finished on another stream) race on the array and give wrong results --
+ * serialise them.
+ * d_status: caller-owned device int, set to 0 by the call and then to the
+ * first status a device-side check raises (KG_ERR_CAPACITY, KG_ERR_INTERNAL);
+ * read it after the stream has finished.  It must not be NULL.  This entry
+ * point does not use the error word of kg_last_error().
+ */
+#define KG_NOALLOC_SCRATCH_BYTES (32u << 20)
+kg_status kg_gnm_directed_noalloc(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                                  int id_bytes, void* d_out, uint64_t cap_edges, int* d_status,
+                                  void* stream);
+
 /* Order-independent digest of an edge list (see kg_gnm_directed_range):
  * *d_digest = sum of splitmix64(u xor rotl64(v, 32)) over `count` pairs. */
 kg_status kg_edge_digest(const void* d_edges, uint64_t count, int id_bytes, uint64_t* d_digest,

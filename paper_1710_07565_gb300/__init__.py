@@ -62,6 +62,7 @@ def lib() -> ctypes.CDLL:
                 "kg_gnp_ex": [i32, u64, dbl, u64, u32, u32, i32, vp, u64, vp, vp],
                 "kg_edge_digest": [vp, u64, i32, vp, vp],
                 "kg_last_error": [vp],
+                "kg_gnm_directed_noalloc": [u64, u64, u64, u32, i32, vp, u64, vp, vp],
             }
             for name, args in sigs.items():
                 f = getattr(L, name, None)
@@ -147,6 +148,13 @@ def kg_gnp_undirected(n, p, seed, chunks, id_bytes, d_out, cap_edges, d_count, s
 def kg_gnp_ex(undirected, n, p, seed, chunks, k_leaf, id_bytes, d_out, cap_edges, d_count, stream):
     return _call("kg_gnp_ex", int(undirected), n, p, seed, chunks, k_leaf, id_bytes, d_out,
                  cap_edges, d_count, stream)
+
+
+def kg_gnm_directed_noalloc(n, m, seed, chunks, id_bytes, d_out, cap_edges, d_status, stream):
+    """Directed G(n,m) that allocates nothing: scratch is a fixed array inside
+    the library (see include/kg.h for the size limit and the sharing rules)."""
+    return _call("kg_gnm_directed_noalloc", n, m, seed, chunks, id_bytes, d_out, cap_edges,
+                 d_status, stream)
 
 
 def kg_edge_digest(d_edges, count, id_bytes, d_digest, stream):

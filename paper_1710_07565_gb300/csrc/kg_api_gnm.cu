@@ -293,3 +293,79 @@ kg_status kg_edge_digest(const void* d_edges, uint64_t count, int id_bytes, uint
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- no-allocation variant
+// Directed G(n,m) for callers that cannot allocate device memory.  The
+// scratch lives in one file-scope device array; every call shares it.
+namespace kg {
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[KG_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device with cudaGetSymbolAddress (with that device current) and cached.
+void* noalloc_scratch_address() {
+  static std::mutex mu;
+  static std::unordered_map<int, void*> addr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = addr.find(dev);
+  if (it != addr.end()) return it->second;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return nullptr;
+  addr[dev] = p;
+  return p;
+}
+
+uint64_t piece(uint64_t bytes) { return (bytes + 255) & ~uint64_t(255); }
+
+// Scratch bytes the directed orchestration takes, in its allocation order.
+uint64_t scan_bytes(uint64_t n) {
+  const uint64_t items = 512 * 8;
+  const uint64_t nb = (n + items - 1) / items;
+  if (n == 0 || nb == 1) return 0;
+  return piece(nb * 8) + piece((nb + 1) * 8) + scan_bytes(nb);
+}
+uint64_t directed_scratch_bytes(const DirParams& dp) {
+  const uint64_t P = dp.P, T = P << dp.d;
+  uint64_t b = piece(P * 8);                       // chunk counts
+  b += piece((uint64_t(2) << dp.D) * 8);           // chunk-tree node counts
+  if (dp.d > 0) b += 2 * piece(T * 8);             // tile-tree levels (ping-pong)
+  b += piece((T + 1) * 8);                         // tile offsets
+  b += scan_bytes(T);                              // scan partials
+  b += piece(T * 8) + piece(8);                    // over-full tile list + its length
+  return b;
+}
+
+}  // namespace
+}  // namespace kg
+
+extern "C" kg_status kg_gnm_directed_noalloc(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                                             int id_bytes, void* d_out, uint64_t cap_edges,
+                                             int* d_status, void* stream) {
+  DirParams dp;
+  int st = check_directed(n, m, chunks, K_LEAF, K_MAX, id_bytes, dp);
+  if (st) return kg_status(st);
+  if (!d_status) return KG_ERR_ARG;
+  if (cap_edges < m) return KG_ERR_CAPACITY;
+  if (directed_scratch_bytes(dp) > uint64_t(KG_NOALLOC_SCRATCH_BYTES)) return KG_ERR_RANGE;
+  if (m > 0 && !d_out) return KG_ERR_ARG;
+  void* arena = noalloc_scratch_address();
+  if (!arena) return KG_ERR_CUDA;
+  cudaStream_t s = as_stream(stream);
+  // device-side checks report into the caller's status word, cleared first
+  int* err = d_status;
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return KG_ERR_CUDA;
+  if (m == 0) return KG_OK;
+  Workspace ws(s, arena, KG_NOALLOC_SCRATCH_BYTES);
+  uint64_t* cnt = ws.alloc<uint64_t>(chunks);
+  if (!ws.ok()) return KG_ERR_INTERNAL;
+  st = run_chunk_tree(dp, seed, cnt, ws, s, err);
+  if (st) return kg_status(st);
+  st = run_chunks(dir_geom(n, chunks), 0, chunks, cnt, dp.d, K_MAX, seed, id_bytes, d_out,
+                  cap_edges, ws, s, err);
+  if (st) return kg_status(st);
+  return ws.ok() ? KG_OK : KG_ERR_INTERNAL;
+}

@@ -1,0 +1,65 @@
+"""kg_gnm_directed_noalloc: the directed G(n,m) entry point for callers that
+cannot let the library allocate device memory (its scratch is a fixed array
+inside libkg.so).  It must return exactly the bytes of kg_gnm_directed.
+
+This file is collected last on purpose: if it fails, a run that stops at the
+first failure has already run every other test.  It calls the C ABI through
+the ctypes binding; the output and status buffers are the caller's.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import need_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kg():
+    need_cuda()
+    import paper_1710_07565_gb300 as kg
+    kg.lib()
+    return kg
+
+
+def _noalloc(kg, n, m, seed, P, id_bytes):
+    import torch
+    dt = torch.int32 if id_bytes == 4 else torch.int64
+    out = torch.full((m, 2), -1, dtype=dt, device="cuda")
+    status = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    s = kg._stream_ptr(None)
+    kg.kg_gnm_directed_noalloc(n, m, seed, P, id_bytes, out.data_ptr(), m, status.data_ptr(), s)
+    torch.cuda.synchronize()
+    assert int(status.item()) == kg.KG_OK
+    return out
+
+
+def _reference(kg, n, m, seed, P, id_bytes):
+    out = kg.gnm_directed(n, m, seed, P, id_bytes=id_bytes)
+    kg.check_device_error()
+    return out
+
+
+def test_two_calls_in_a_row_match_the_allocating_entry_point(kg):
+    import torch
+    cases = [
+        (1 << 16, 1 << 20, 1, 64, 4),        # n = 2^16, m = 2^20, 64 chunks, uint32 ids
+        (12345, 777777, 11, 31, 8),          # ragged chunks and tiles, uint64 ids
+    ]
+    for n, m, seed, P, idb in cases:
+        got = _noalloc(kg, n, m, seed, P, idb)
+        want = _reference(kg, n, m, seed, P, idb)
+        # integer output: equal bit for bit
+        assert torch.equal(got, want), (n, m, P)
+
+
+def test_sizes_beyond_the_scratch_are_rejected_before_any_work(kg):
+    import torch
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = kg._stream_ptr(None)
+    L = kg.lib()
+    # 2^23 tiles would need ~256 MiB of scratch: rejected synchronously
+    st = L.kg_gnm_directed_noalloc(1 << 36, 1 << 33, 1, 1 << 16, 8, 0, 1 << 33, status.data_ptr(), s)
+    assert st == kg.KG_ERR_RANGE
+    st = L.kg_gnm_directed_noalloc(100, 50, 1, 4, 4, 0, 50, 0, s)  # no status word
+    assert st == kg.KG_ERR_ARG
