@@ -5,9 +5,7 @@
 
 #include "../../include/kg.h"
 #include "kg_digest.cuh"
-#include "kg_leaf.cuh"
-#include "kg_internal.h"
-#include "kg_prof.h"
+#include "kg_run.cuh"
 
 namespace kg {
 
@@ -31,113 +29,6 @@ int* device_error_word() {
   }
   words[dev] = p;
   return p;
-}
-
-// Tile-tree depth, one per instance: smallest d with E <= k_leaf 2^d, where
-// E = m (U_nom / N) is the expected count of a chunk of nominal universe U_nom.
-int tile_depth(uint64_t m, u128 Unom, u128 Ntot, uint32_t k_leaf, int& d_out) {
-  const double E = double(m) * (dbl(Unom) / dbl(Ntot));
-  int d = 0;
-  for (;;) {
-    if (E <= double(k_leaf) * double(uint64_t(1) << d)) break;
-    if ((u128(2) << d) > Unom) break;
-    if (d == D_MAX) return ST_RANGE;
-    ++d;
-  }
-  d_out = d;
-  return ST_OK;
-}
-
-static unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
-  uint64_t b = (items + per_block - 1) / per_block;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return unsigned(b);
-}
-
-static int launch_ok() { return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA; }
-
-// Tile trees + scan + leaves for chunks [c_begin, c_begin + C) of a geometry.
-// level0: the chunks' counts (device).  Pairs go to d_out[0 ..).  With digest
-// pointers the leaf kernel also produces the per-chunk digest and out-degree
-// histogram (directed geometry only).
-template <class Geom, class Sink, bool DIGEST>
-static int launch_leaf(const Geom& g, const Sink& sink, uint64_t c_begin, int d, uint32_t k_max,
-                       uint64_t seed, const uint64_t* tile_cnt, const uint64_t* tile_off,
-                       uint64_t T, int* err, DigestOut dig, Workspace& ws, cudaStream_t s) {
-  unsigned long long* big = ws.alloc<unsigned long long>(T);
-  unsigned long long* nbig = ws.alloc<unsigned long long>(1);
-  if (!ws.ok()) return ST_CUDA;
-  if (cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), s) != cudaSuccess) return ST_CUDA;
-  const unsigned grid = unsigned(T < 0x7fffffffull ? T : 0x7fffffffull);
-  {
-    ProfScope ps(PROF_LEAF, s);
-    leaf_fast_kernel<Geom, Sink, DIGEST><<<grid, FAST_THREADS, 0, s>>>(
-        g, sink, c_begin, d, k_max, seed, round_keys(seed), tile_cnt, tile_off, T, err, dig, big,
-        nbig);
-    if (launch_ok()) return ST_CUDA;
-  }
-  ProfScope ps(PROF_OTHER, s);
-  leaf_resplit_kernel<Geom, Sink, DIGEST><<<152, LEAF_THREADS, 0, s>>>(
-      g, sink, c_begin, d, k_max, seed, tile_cnt, tile_off, err, dig, big, nbig);
-  return launch_ok();
-}
-
-template <class Geom>
-int run_chunks(const Geom& g, uint64_t c_begin, uint64_t C, const uint64_t* level0, int d,
-               uint32_t k_max, uint64_t seed, int id_bytes, void* d_out, uint64_t cap,
-               Workspace& ws, cudaStream_t s, int* err, uint64_t* digest = nullptr,
-               uint64_t* hist = nullptr) {
-  const uint64_t T = C << d;
-  const uint64_t* in = level0;
-  if (d > 0) {
-    uint64_t* A = ws.alloc<uint64_t>(T);
-    uint64_t* B = ws.alloc<uint64_t>(T);
-    if (!ws.ok()) return ST_CUDA;
-    for (int level = 0; level < d; ++level) {
-      uint64_t* out = (level & 1) ? B : A;
-      const uint64_t nodes = C << level;
-      ProfScope ps(PROF_TILE_TREE, s);
-      tile_tree_level<Geom><<<grid_for(nodes, 256, 152 * 16), 256, 0, s>>>(
-          g, c_begin, C, d, level, seed, in, out, err);
-      if (launch_ok()) return ST_CUDA;
-      in = out;
-    }
-  }
-  uint64_t* tile_off = ws.alloc<uint64_t>(T + 1);
-  if (!ws.ok()) return ST_CUDA;
-  int st = scan_exclusive_u64(in, tile_off, T, ws, s);
-  if (st) return st;
-  const bool want = digest || hist;
-  DigestOut dig{nullptr, nullptr, nullptr};
-  if (want) {
-    dig.digest = reinterpret_cast<unsigned long long*>(digest ? digest : ws.alloc<uint64_t>(C));
-    dig.hist = reinterpret_cast<unsigned long long*>(hist ? hist : ws.alloc<uint64_t>(C * 65));
-    dig.rec = ws.alloc<TileRec>(T);
-    if (!ws.ok()) return ST_CUDA;
-    if (cudaMemsetAsync(dig.digest, 0, C * sizeof(uint64_t), s) != cudaSuccess ||
-        cudaMemsetAsync(dig.hist, 0, C * 65 * sizeof(uint64_t), s) != cudaSuccess ||
-        cudaMemsetAsync(dig.rec, 0, T * sizeof(TileRec), s) != cudaSuccess)
-      return ST_CUDA;
-  }
-  if (id_bytes == 4) {
-    PairSink<uint32_t> sink{static_cast<uint32_t*>(d_out), cap, err};
-    st = want ? launch_leaf<Geom, PairSink<uint32_t>, true>(g, sink, c_begin, d, k_max, seed, in,
-                                                             tile_off, T, err, dig, ws, s)
-              : launch_leaf<Geom, PairSink<uint32_t>, false>(g, sink, c_begin, d, k_max, seed, in,
-                                                              tile_off, T, err, dig, ws, s);
-  } else {
-    PairSink<uint64_t> sink{static_cast<uint64_t*>(d_out), cap, err};
-    st = want ? launch_leaf<Geom, PairSink<uint64_t>, true>(g, sink, c_begin, d, k_max, seed, in,
-                                                             tile_off, T, err, dig, ws, s)
-              : launch_leaf<Geom, PairSink<uint64_t>, false>(g, sink, c_begin, d, k_max, seed, in,
-                                                              tile_off, T, err, dig, ws, s);
-  }
-  if (st || !want) return st;
-  ProfScope ps(PROF_DIGEST, s);
-  chunk_run_merge<Geom><<<grid_for(C, 128, 152 * 8), 128, 0, s>>>(g, c_begin, C, d, dig.rec,
-                                                                   dig.hist);
-  return launch_ok();
 }
 
 // ---------------------------------------------------------------- directed

@@ -1,0 +1,292 @@
+// C ABI: undirected G(n,m) (Sec. 4.2) and G(n,p) (Sec. 4.3), directed and
+// undirected, with the assembly of undirected output in both directions.
+#include "../../include/kg.h"
+#include "kg_gnp.cuh"
+#include "kg_run.cuh"
+#include "kg_und.cuh"
+
+namespace kg {
+
+static cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+// pairs (u > v) -> both directions, sorted by (u, v), into out[0 .. 2 npairs)
+template <class Id>
+static int assemble(const Id* pairs, const uint64_t* npairs_dev, uint64_t npairs_host, uint64_t n,
+                    Id* out, uint64_t cap, Workspace& ws, cudaStream_t s, int* err) {
+  unsigned long long* deg = ws.alloc<unsigned long long>(n);
+  uint64_t* rowptr = ws.alloc<uint64_t>(n + 1);
+  unsigned long long* cursor = ws.alloc<unsigned long long>(n);
+  unsigned long long* long_rows = ws.alloc<unsigned long long>(n);
+  unsigned long long* nlong = ws.alloc<unsigned long long>(1);
+  if (!ws.ok()) return ST_CUDA;
+  if (cudaMemsetAsync(deg, 0, n * 8, s) != cudaSuccess ||
+      cudaMemsetAsync(nlong, 0, 8, s) != cudaSuccess)
+    return ST_CUDA;
+  const uint64_t work = npairs_dev ? cap / 2 : npairs_host;
+  {
+    ProfScope ps(PROF_ASSEMBLY, s);
+    und_degree<Id><<<grid_for(work, 256, 152 * 16), 256, 0, s>>>(pairs, npairs_dev, npairs_host,
+                                                                 deg);
+    if (launch_ok()) return ST_CUDA;
+  }
+  int st = scan_exclusive_u64(reinterpret_cast<const uint64_t*>(deg), rowptr, n, ws, s);
+  if (st) return st;
+  if (cudaMemcpyAsync(cursor, rowptr, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return ST_CUDA;
+  {
+    ProfScope ps(PROF_ASSEMBLY, s);
+    und_scatter<Id><<<grid_for(work, 256, 152 * 16), 256, 0, s>>>(pairs, npairs_dev, npairs_host,
+                                                                  cursor, out, cap, err);
+    if (launch_ok()) return ST_CUDA;
+  }
+  {
+    ProfScope ps(PROF_ASSEMBLY, s);
+    und_sort_short<Id><<<grid_for(n, 8, 152 * 32), 256, 0, s>>>(rowptr, n, out, cap, long_rows,
+                                                                nlong);
+    if (launch_ok()) return ST_CUDA;
+  }
+  ProfScope ps(PROF_ASSEMBLY, s);
+  und_sort_long<Id><<<152 * 2, 256, 0, s>>>(rowptr, out, cap, long_rows, nlong);
+  return launch_ok();
+}
+
+// ---------------------------------------------------------------- undirected G(n,m)
+struct UndParams {
+  uint64_t n, m;
+  uint32_t P;
+  u128 Ntot, Unom;
+  int d, D;
+};
+
+static int check_undirected(uint64_t n, uint64_t m, uint32_t P, uint32_t k_leaf, uint32_t k_max,
+                            int id_bytes, UndParams& up) {
+  if (n == 0 || P == 0 || uint64_t(P) > n) return ST_ARG;
+  if (id_bytes != 4 && id_bytes != 8) return ST_ARG;
+  if (k_leaf < 2 || k_max < k_leaf || k_max > uint32_t(K_MAX)) return ST_ARG;
+  up.n = n;
+  up.m = m;
+  up.P = P;
+  up.Ntot = tri_pairs(n);
+  if (u128(m) > up.Ntot) return ST_ARG;
+  if (m > M_MAX || P > 65536u || n > (uint64_t(1) << 31)) return ST_RANGE;
+  const u128 rmax = (u128(n) + P - 1) / P;
+  up.Unom = rmax * rmax;
+  int st = tile_depth(m, up.Unom, up.Ntot, k_leaf, up.d);
+  if (st) return st;
+  up.D = 0;
+  while ((uint64_t(1) << up.D) < P) ++up.D;
+  return ST_OK;
+}
+
+// Quadrant recursion: levels 0..D, node lists ping-pong, leaf counts per chunk.
+static int run_quadtree(const UndParams& up, uint64_t seed, uint64_t* chunk_cnt, Workspace& ws,
+                        cudaStream_t s, int* err) {
+  const uint64_t C = uint64_t(up.P) * (up.P + 1) / 2;
+  QNode* L0 = ws.alloc<QNode>(C);
+  QNode* L1 = ws.alloc<QNode>(C);
+  uint32_t* counts = ws.alloc<uint32_t>(up.D + 2);
+  if (!ws.ok()) return ST_CUDA;
+  const RowBounds rb = RowBounds::make(up.n, up.P);
+  {
+    ProfScope ps(PROF_CHUNK_TREE, s);
+    quad_init<<<1, 32, 0, s>>>(L0, counts, up.D + 1, up.P, up.m);
+    if (launch_ok()) return ST_CUDA;
+  }
+  for (int l = 0; l <= up.D; ++l) {
+    const uint64_t bound = (l < 16) ? ((uint64_t(1) << l) * ((uint64_t(1) << l) + 1) / 2) : C;
+    ProfScope ps(PROF_CHUNK_TREE, s);
+    quad_level<<<grid_for(bound < C ? bound : C, 256, 152 * 8), 256, 0, s>>>(
+        rb, seed, (l & 1) ? L1 : L0, counts + l, (l & 1) ? L0 : L1, counts + l + 1, chunk_cnt, err);
+    if (launch_ok()) return ST_CUDA;
+  }
+  return ST_OK;
+}
+
+template <class Id>
+static int gnm_undirected_impl(const UndParams& up, uint64_t seed, uint32_t k_max, void* d_out,
+                               uint64_t cap, cudaStream_t s, int* err) {
+  Workspace ws(s);
+  const uint64_t C = uint64_t(up.P) * (up.P + 1) / 2;
+  uint64_t* chunk_cnt = ws.alloc<uint64_t>(C);
+  Id* pairs = ws.alloc<Id>(2 * up.m);
+  if (!ws.ok()) return ST_CUDA;
+  int st = run_quadtree(up, seed, chunk_cnt, ws, s, err);
+  if (st) return st;
+  UndGeom g{up.n, up.P, RowBounds::make(up.n, up.P)};
+  st = run_chunks(g, 0, C, chunk_cnt, up.d, k_max, seed, int(sizeof(Id)), pairs, up.m, ws, s, err);
+  if (st) return st;
+  return assemble<Id>(pairs, nullptr, up.m, up.n, static_cast<Id*>(d_out), cap, ws, s, err);
+}
+
+// ---------------------------------------------------------------- G(n,p)
+static uint64_t gnp_tile_len(double p, uint32_t k_leaf) {
+  const double q = double(k_leaf) / p;
+  if (!(q >= 2.0)) return 1;
+  uint64_t T = 1;
+  while (T < (uint64_t(1) << 62) && double(T * 2) <= q) T *= 2;
+  return T;
+}
+
+__global__ void gnp_total(const uint64_t* off_end, uint64_t* d_count, uint64_t* npairs,
+                          uint64_t mult, uint64_t cap, int* err) {
+  const uint64_t tot = *off_end;
+  *d_count = tot * mult;
+  if (npairs) *npairs = (tot * mult <= cap) ? tot : cap / mult;
+  if (tot * mult > cap) set_error(err, ST_CAPACITY);
+}
+
+template <class Geom, class Id, class SlotT>
+static int gnp_impl(const Geom& g, uint64_t C, bool undirected, uint64_t n, const GnpPlan& pl,
+                    uint64_t seed, void* d_out, uint64_t cap, uint64_t* d_count, cudaStream_t s,
+                    int* err) {
+  Workspace ws(s);
+  const uint64_t tiles = C * pl.tiles_per_chunk;
+  SlotT* slots = pl.cap_t ? ws.alloc<SlotT>(tiles * pl.cap_t) : nullptr;
+  uint64_t* cnt = ws.alloc<uint64_t>(tiles);
+  uint64_t* off = ws.alloc<uint64_t>(tiles + 1);
+  uint64_t* npairs = ws.alloc<uint64_t>(1);
+  if (!ws.ok()) return ST_CUDA;
+  {
+    ProfScope ps(PROF_GNP, s);
+    gnp_tiles<Geom, SlotT><<<grid_for(tiles, 128, 1u << 20), 128, 0, s>>>(g, pl, seed, C, slots,
+                                                                          cnt);
+    if (launch_ok()) return ST_CUDA;
+  }
+  int st = scan_exclusive_u64(cnt, off, tiles, ws, s);
+  if (st) return st;
+  const uint64_t mult = undirected ? 2 : 1;
+  {
+    ProfScope ps(PROF_OTHER, s);
+    gnp_total<<<1, 1, 0, s>>>(off + tiles, d_count, npairs, mult, cap, err);
+    if (launch_ok()) return ST_CUDA;
+  }
+  if (!undirected) {
+    PairSink<Id> sink{static_cast<Id*>(d_out), cap, err};
+    ProfScope ps(PROF_LEAF, s);
+    gnp_emit<Geom, SlotT, PairSink<Id>><<<grid_for(tiles, 4, 152 * 64), 128, 0, s>>>(
+        g, pl, seed, C, slots, cnt, off, sink);
+    return launch_ok();
+  }
+  const uint64_t pcap = cap / 2;
+  Id* pairs = ws.alloc<Id>(2 * (pcap ? pcap : 1));
+  if (!ws.ok()) return ST_CUDA;
+  {
+    // pairs beyond pcap are dropped by the sink without an error: the total
+    // check above already recorded the capacity error
+    PairSink<Id> sink{pairs, pcap, nullptr};
+    ProfScope ps(PROF_LEAF, s);
+    gnp_emit<Geom, SlotT, PairSink<Id>><<<grid_for(tiles, 4, 152 * 64), 128, 0, s>>>(
+        g, pl, seed, C, slots, cnt, off, sink);
+    if (launch_ok()) return ST_CUDA;
+  }
+  return assemble<Id>(pairs, npairs, 0, n, static_cast<Id*>(d_out), cap, ws, s, err);
+}
+
+template <class Geom, class Id>
+static int gnp_dispatch_slots(const Geom& g, uint64_t C, bool und, uint64_t n, const GnpPlan& pl,
+                              uint64_t seed, void* d_out, uint64_t cap, uint64_t* d_count,
+                              cudaStream_t s, int* err) {
+  if (pl.T <= (uint64_t(1) << 32))
+    return gnp_impl<Geom, Id, uint32_t>(g, C, und, n, pl, seed, d_out, cap, d_count, s, err);
+  return gnp_impl<Geom, Id, uint64_t>(g, C, und, n, pl, seed, d_out, cap, d_count, s, err);
+}
+
+}  // namespace kg
+
+using namespace kg;
+
+extern "C" {
+
+kg_status kg_gnm_undirected_ex(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                               uint32_t k_leaf, uint32_t k_max, int id_bytes, void* d_out,
+                               uint64_t cap_edges, void* stream) {
+  UndParams up;
+  int st = check_undirected(n, m, chunks, k_leaf, k_max, id_bytes, up);
+  if (st) return kg_status(st);
+  if (cap_edges < 2 * m) return KG_ERR_CAPACITY;
+  if (m == 0) return KG_OK;
+  if (!d_out) return KG_ERR_ARG;
+  int* err = device_error_word();
+  if (!err) return KG_ERR_CUDA;
+  cudaStream_t s = as_stream(stream);
+  st = id_bytes == 4 ? gnm_undirected_impl<uint32_t>(up, seed, k_max, d_out, cap_edges, s, err)
+                     : gnm_undirected_impl<uint64_t>(up, seed, k_max, d_out, cap_edges, s, err);
+  return kg_status(st);
+}
+
+kg_status kg_gnm_undirected(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks, int id_bytes,
+                            void* d_out, uint64_t cap_edges, void* stream) {
+  return kg_gnm_undirected_ex(n, m, seed, chunks, K_LEAF, K_MAX, id_bytes, d_out, cap_edges,
+                              stream);
+}
+
+kg_status kg_gnp_ex(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
+                    uint32_t k_leaf, int id_bytes, void* d_out, uint64_t cap_edges,
+                    uint64_t* d_count, void* stream) {
+  if (!(p >= 0.0 && p <= 1.0) || k_leaf < 2 || !d_count) return KG_ERR_ARG;
+  if (n == 0 || chunks == 0 || uint64_t(chunks) > n) return KG_ERR_ARG;
+  if (id_bytes != 4 && id_bytes != 8) return KG_ERR_ARG;
+  if (id_bytes == 4 && n > (uint64_t(1) << 32)) return KG_ERR_RANGE;
+  const uint64_t rows_max = uint64_t((u128(n) + chunks - 1) / chunks);
+  u128 Unom;
+  uint64_t C;
+  if (undirected) {
+    if (chunks > 65536u || n > (uint64_t(1) << 31)) return KG_ERR_RANGE;
+    Unom = u128(rows_max) * rows_max;
+    C = uint64_t(chunks) * (chunks + 1) / 2;
+  } else {
+    if (chunks > (1u << 24)) return KG_ERR_RANGE;
+    Unom = u128(rows_max) * (n - 1);
+    C = chunks;
+  }
+  if (Unom >> 64) return KG_ERR_RANGE;
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s) != cudaSuccess) return KG_ERR_CUDA;
+  if (p == 0.0 || n < 2) return KG_OK;
+  GnpPlan pl;
+  pl.p = p;
+  pl.all = (p >= 1.0);
+  pl.inv_lq = pl.all ? 0.0 : 1.0 / kg_log1m(p);
+  pl.T = pl.all ? (uint64_t(1) << 20) : gnp_tile_len(p, k_leaf);
+  pl.tiles_per_chunk = uint64_t((Unom + pl.T - 1) / pl.T);
+  if (pl.tiles_per_chunk > (uint64_t(1) << 32)) return KG_ERR_RANGE;
+  const u128 tiles = u128(C) * pl.tiles_per_chunk;
+  if (tiles > (u128(1) << 34)) return KG_ERR_RANGE;
+  uint64_t cap_t = pl.all ? 0 : 2 * uint64_t(k_leaf) + 64;
+  if (cap_t > pl.T) cap_t = pl.T;
+  const uint64_t slot_bytes = (pl.T <= (uint64_t(1) << 32)) ? 4 : 8;
+  if (uint64_t(tiles) * cap_t * slot_bytes > (uint64_t(4) << 30)) cap_t = 0;  // regenerate tiles
+  pl.cap_t = uint32_t(cap_t);
+  if (!d_out && cap_edges > 0) return KG_ERR_ARG;
+  int* err = device_error_word();
+  if (!err) return KG_ERR_CUDA;
+  int st;
+  if (undirected) {
+    UndGeom g{n, chunks, RowBounds::make(n, chunks)};
+    st = id_bytes == 4
+             ? gnp_dispatch_slots<UndGeom, uint32_t>(g, C, true, n, pl, seed, d_out, cap_edges, d_count, s, err)
+             : gnp_dispatch_slots<UndGeom, uint64_t>(g, C, true, n, pl, seed, d_out, cap_edges, d_count, s, err);
+  } else {
+    DirGeom g;
+    g.n = n;
+    g.P = chunks;
+    g.div = make_div(n - 1);
+    g.rb = RowBounds::make(n, chunks);
+    st = id_bytes == 4
+             ? gnp_dispatch_slots<DirGeom, uint32_t>(g, C, false, n, pl, seed, d_out, cap_edges, d_count, s, err)
+             : gnp_dispatch_slots<DirGeom, uint64_t>(g, C, false, n, pl, seed, d_out, cap_edges, d_count, s, err);
+  }
+  return kg_status(st);
+}
+
+kg_status kg_gnp_directed(uint64_t n, double p, uint64_t seed, uint32_t chunks, int id_bytes,
+                          void* d_out, uint64_t cap_edges, uint64_t* d_count, void* stream) {
+  return kg_gnp_ex(0, n, p, seed, chunks, K_LEAF, id_bytes, d_out, cap_edges, d_count, stream);
+}
+
+kg_status kg_gnp_undirected(uint64_t n, double p, uint64_t seed, uint32_t chunks, int id_bytes,
+                            void* d_out, uint64_t cap_edges, uint64_t* d_count, void* stream) {
+  return kg_gnp_ex(1, n, p, seed, chunks, K_LEAF, id_bytes, d_out, cap_edges, d_count, stream);
+}
+
+}  // extern "C"

@@ -89,6 +89,12 @@ struct UndGeom {
     ij(k, i, j);
     return uint64_t(i) * P + j;
   }
+  // rows of the chunk's row block
+  __host__ __device__ __forceinline__ uint64_t rows(uint64_t k) const {
+    uint32_t i, j;
+    ij(k, i, j);
+    return rb(uint64_t(i) + 1) - rb(i);
+  }
   __host__ __device__ __forceinline__ uint64_t universe(uint64_t k) const {
     uint32_t i, j;
     ij(k, i, j);

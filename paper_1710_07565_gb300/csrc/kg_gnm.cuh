@@ -27,7 +27,7 @@ __device__ __forceinline__ bool chunk_range(uint32_t P, uint64_t h, int level, u
 // Levels [l0, l1) of the directed chunk tree, one block per subtree rooted at
 // level l0.  Node h with range [a,b) and count mc splits at s = a + ceil((b-a)/2)
 // (l = ceil(P/2)) by X = Hyp(rows[a,b)(n-1), rows[a,s)(n-1), mc).
-__global__ void chunk_tree_band(RowBounds rb, uint64_t seed, uint64_t m, int l0, int l1,
+static __global__ void chunk_tree_band(RowBounds rb, uint64_t seed, uint64_t m, int l0, int l1,
                                 uint64_t* __restrict__ node_cnt, uint64_t* __restrict__ cnt,
                                 int* err) {
   const uint64_t n = rb.n;

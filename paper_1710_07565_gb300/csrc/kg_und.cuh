@@ -1,0 +1,272 @@
+// Undirected generators (Sec. 4.2): the quadrant recursion over the
+// triangular P x P chunk matrix, and the assembly of the sampled lower-triangle
+// pairs into one (u, v)-sorted list holding every edge in both directions.
+#pragma once
+#include "kg_common.cuh"
+
+namespace kg {
+
+// ---------------------------------------------------------------- quadrant tree
+// A node is a triangle of blocks [a, b) (a == c, b == d) or a rectangle of
+// row blocks [a, b) x column blocks [c, d) strictly below the diagonal.
+struct QNode {
+  uint32_t a, b, c, d;
+  uint64_t cnt;
+};
+
+__host__ __device__ __forceinline__ uint64_t quad_id(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  return uint64_t(a) | (uint64_t(b - 1) << 16) | (uint64_t(c) << 32) | (uint64_t(d - 1) << 48);
+}
+__host__ __device__ __forceinline__ u128 tri_pairs(uint64_t S) {
+  return S ? u128(S) * (S - 1) / 2 : 0;
+}
+__host__ __device__ __forceinline__ uint64_t und_chunk_index(uint32_t i, uint32_t j) {
+  return uint64_t(i) * (i + 1) / 2 + j;
+}
+
+static __global__ void quad_init(QNode* list, uint32_t* counts, int nlevels, uint32_t P, uint64_t m) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    list[0] = QNode{0, P, 0, P, m};
+    counts[0] = 1;
+    for (int l = 1; l <= nlevels; ++l) counts[l] = 0;
+  }
+}
+
+// One level: every node either is a chunk (its count is final) or draws its
+// parts' counts from its own stream, in order, and appends the parts.
+//  - triangle [a,b), l = ceil((b-a)/2): T1 = tri[a,a+l), R = rows [a+l,b) x
+//    cols [a,a+l), T2 = tri[a+l,b); X1 = Hyp(N, |T1|, cnt),
+//    X2 = Hyp(N - |T1|, |R|, cnt - X1), T2 gets the rest;
+//  - rectangle: each dimension with more than one block halved at ceil, the
+//    parts in row-major order, sequential conditional hypergeometrics.
+static __global__ void __launch_bounds__(256)
+    quad_level(RowBounds rb, uint64_t seed, const QNode* __restrict__ in,
+               const uint32_t* __restrict__ nin, QNode* __restrict__ out, uint32_t* nout,
+               uint64_t* __restrict__ chunk_cnt, int* err) {
+  const uint32_t count = *nin;
+  for (uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x; idx < count;
+       idx += gridDim.x * blockDim.x) {
+    const QNode q = in[idx];
+    const bool tri = (q.a == q.c && q.b == q.d);
+    if (tri && q.b - q.a == 1) {
+      chunk_cnt[und_chunk_index(q.a, q.a)] = q.cnt;
+      continue;
+    }
+    if (!tri && q.b - q.a == 1 && q.d - q.c == 1) {
+      chunk_cnt[und_chunk_index(q.a, q.c)] = q.cnt;
+      continue;
+    }
+    Stream st(seed, quad_id(q.a, q.b, q.c, q.d), TAG_QUAD);
+    if (tri) {
+      const uint32_t l = (q.b - q.a + 1) / 2;
+      const uint64_t ra = rb(q.a), rm = rb(q.a + l), rbb = rb(q.b);
+      const uint64_t S1 = rm - ra, S2 = rbb - rm;
+      const u128 T1 = tri_pairs(S1), R = u128(S2) * S1, T2 = tri_pairs(S2);
+      const u128 N = T1 + R + T2;
+      uint64_t X1 = 0, X2 = 0;
+      int e = hypergeometric(N, T1, q.cnt, st, X1);
+      if (!e) e = hypergeometric(N - T1, R, q.cnt - X1, st, X2);
+      if (e) {
+        set_error(err, e);
+        X1 = X2 = 0;
+      }
+      const uint32_t o = atomicAdd(nout, 3u);
+      out[o] = QNode{q.a, q.a + l, q.a, q.a + l, X1};
+      out[o + 1] = QNode{q.a + l, q.b, q.a, q.a + l, X2};
+      out[o + 2] = QNode{q.a + l, q.b, q.a + l, q.b, q.cnt - X1 - X2};
+      continue;
+    }
+    uint32_t rlo[2] = {q.a, 0}, rhi[2] = {q.b, 0}, clo[2] = {q.c, 0}, chi[2] = {q.d, 0};
+    int nr = 1, nc = 1;
+    if (q.b - q.a >= 2) {
+      const uint32_t s = q.a + (q.b - q.a + 1) / 2;
+      rhi[0] = s;
+      rlo[1] = s;
+      rhi[1] = q.b;
+      nr = 2;
+    }
+    if (q.d - q.c >= 2) {
+      const uint32_t s = q.c + (q.d - q.c + 1) / 2;
+      chi[0] = s;
+      clo[1] = s;
+      chi[1] = q.d;
+      nc = 2;
+    }
+    QNode parts[4];
+    u128 size[4];
+    int np = 0;
+    u128 N = 0;
+    for (int i = 0; i < nr; ++i)
+      for (int j = 0; j < nc; ++j) {
+        parts[np] = QNode{rlo[i], rhi[i], clo[j], chi[j], 0};
+        size[np] = u128(rb(rhi[i]) - rb(rlo[i])) * (rb(chi[j]) - rb(clo[j]));
+        N += size[np];
+        ++np;
+      }
+    uint64_t rem = q.cnt;
+    for (int i = 0; i < np - 1; ++i) {
+      uint64_t X = 0;
+      const int e = hypergeometric(N, size[i], rem, st, X);
+      if (e) {
+        set_error(err, e);
+        X = 0;
+      }
+      parts[i].cnt = X;
+      N -= size[i];
+      rem -= X;
+    }
+    parts[np - 1].cnt = rem;
+    const uint32_t o = atomicAdd(nout, uint32_t(np));
+    for (int i = 0; i < np; ++i) out[o + i] = parts[i];
+  }
+}
+
+// ---------------------------------------------------------------- assembly
+// The sampled pairs (u > v) of all chunks become the (u, v)-sorted list of
+// both directions: degrees, row offsets (scan), scatter to row slots, and a
+// sort of each row by v.  The rows' contents are unique, so the result does
+// not depend on the order in which the scatter fills a row.
+template <class Id>
+__device__ __forceinline__ void load_pair(const Id* p, uint64_t i, uint64_t& u, uint64_t& v) {
+  u = p[2 * i];
+  v = p[2 * i + 1];
+}
+
+template <class Id>
+__global__ void und_degree(const Id* __restrict__ pairs, const uint64_t* __restrict__ npairs_dev,
+                           uint64_t npairs_host, unsigned long long* __restrict__ deg) {
+  const uint64_t np = npairs_dev ? *npairs_dev : npairs_host;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np;
+       i += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t u, v;
+    load_pair(pairs, i, u, v);
+    atomicAdd(&deg[u], 1ull);
+    atomicAdd(&deg[v], 1ull);
+  }
+}
+
+template <class Id>
+__global__ void und_scatter(const Id* __restrict__ pairs, const uint64_t* __restrict__ npairs_dev,
+                            uint64_t npairs_host, unsigned long long* __restrict__ cursor,
+                            Id* __restrict__ out, uint64_t cap, int* err) {
+  const uint64_t np = npairs_dev ? *npairs_dev : npairs_host;
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np;
+       i += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t u, v;
+    load_pair(pairs, i, u, v);
+    const uint64_t p = atomicAdd(&cursor[u], 1ull);
+    const uint64_t q = atomicAdd(&cursor[v], 1ull);
+    if (p < cap) {
+      out[2 * p] = Id(u);
+      out[2 * p + 1] = Id(v);
+    } else {
+      set_error(err, ST_CAPACITY);
+    }
+    if (q < cap) {
+      out[2 * q] = Id(v);
+      out[2 * q + 1] = Id(u);
+    } else {
+      set_error(err, ST_CAPACITY);
+    }
+  }
+}
+
+// Rows of at most 32 entries: one warp per row, bitonic sort across the lanes.
+// Longer rows are listed for und_sort_long.
+template <class Id>
+__global__ void __launch_bounds__(256)
+    und_sort_short(const uint64_t* __restrict__ rowptr, uint64_t n, Id* __restrict__ out,
+                   uint64_t cap, unsigned long long* long_rows, unsigned long long* nlong) {
+  const unsigned lane = threadIdx.x & 31;
+  const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t u = warp; u < n; u += nwarps) {
+    const uint64_t b = rowptr[u], e = rowptr[u + 1] < cap ? rowptr[u + 1] : cap;
+    if (e <= b) continue;
+    const uint64_t deg = e - b;
+    if (deg > 32) {
+      if (lane == 0) long_rows[atomicAdd(nlong, 1ull)] = u;
+      continue;
+    }
+    uint64_t x = lane < deg ? uint64_t(out[2 * (b + lane) + 1]) : ~uint64_t(0);
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        const bool up = ((lane & k) == 0);
+        const bool lower = ((lane & j) == 0);
+        const uint64_t mn = x < y ? x : y, mx = x < y ? y : x;
+        x = (lower == up) ? mn : mx;
+      }
+    }
+    if (lane < deg) out[2 * (b + lane) + 1] = Id(x);
+  }
+}
+
+constexpr int LONG_SMEM = 4096;
+
+// One block per listed row: a sorting network whose comparisons all move the
+// smaller value to the lower index (first step of each merge compares mirrored
+// positions), so positions past the row behave as +infinity and are never
+// touched.  Rows up to LONG_SMEM entries are sorted in shared memory, longer
+// ones in place in global memory.
+template <class Id>
+__global__ void __launch_bounds__(256)
+    und_sort_long(const uint64_t* __restrict__ rowptr, Id* __restrict__ out, uint64_t cap,
+                  const unsigned long long* __restrict__ long_rows,
+                  const unsigned long long* __restrict__ nlong) {
+  __shared__ uint64_t sh[LONG_SMEM];
+  const unsigned long long nl = *nlong;
+  for (unsigned long long r = blockIdx.x; r < nl; r += gridDim.x) {
+    const uint64_t u = long_rows[r];
+    const uint64_t b = rowptr[u], e = rowptr[u + 1] < cap ? rowptr[u + 1] : cap;
+    const uint64_t deg = e - b;
+    uint64_t N = 1;
+    while (N < deg) N <<= 1;
+    const bool in_smem = deg <= LONG_SMEM;
+    if (in_smem)
+      for (uint64_t i = threadIdx.x; i < deg; i += blockDim.x) sh[i] = out[2 * (b + i) + 1];
+    __syncthreads();
+    auto get = [&](uint64_t i) -> uint64_t { return in_smem ? sh[i] : uint64_t(out[2 * (b + i) + 1]); };
+    auto put = [&](uint64_t i, uint64_t x) {
+      if (in_smem)
+        sh[i] = x;
+      else
+        out[2 * (b + i) + 1] = Id(x);
+    };
+    for (uint64_t k = 2; k <= N; k <<= 1) {
+      for (uint64_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
+        const uint64_t blk = i / (k / 2), off = i % (k / 2);
+        const uint64_t lo = blk * k + off, hi = blk * k + k - 1 - off;
+        if (hi < deg) {
+          const uint64_t x = get(lo), y = get(hi);
+          if (y < x) {
+            put(lo, y);
+            put(hi, x);
+          }
+        }
+      }
+      __syncthreads();
+      for (uint64_t j = k / 4; j >= 1; j >>= 1) {
+        for (uint64_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
+          const uint64_t blk = i / j, off = i % j;
+          const uint64_t lo = blk * 2 * j + off, hi = lo + j;
+          if (hi < deg) {
+            const uint64_t x = get(lo), y = get(hi);
+            if (y < x) {
+              put(lo, y);
+              put(hi, x);
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (in_smem)
+      for (uint64_t i = threadIdx.x; i < deg; i += blockDim.x) out[2 * (b + i) + 1] = Id(sh[i]);
+    __syncthreads();
+  }
+}
+
+}  // namespace kg

@@ -33,11 +33,12 @@ void sh_divq(uint64_t D, const uint64_t* x, uint64_t* q, uint64_t count) {
   for (uint64_t i = 0; i < count; ++i) q[i] = div_q(d, x[i]);
 }
 void sh_und_map(uint64_t n, uint32_t P, uint64_t k, uint64_t off, uint64_t* u, uint64_t* v) {
-  UndGeom g{n, P};
+  UndGeom g{n, P, RowBounds::make(n, P)};
   g.map(g.ctx(k), off, *u, *v);
 }
 uint64_t sh_und_universe(uint64_t n, uint32_t P, uint64_t k) {
-  UndGeom g{n, P};
+  UndGeom g{n, P, RowBounds::make(n, P)};
   return g.universe(k);
 }
+uint64_t sh_row_bound(uint64_t n, uint32_t P, uint64_t c) { return RowBounds::make(n, P)(c); }
 }

@@ -129,3 +129,16 @@ def test_undirected_geometry(sh):
                     sh.sh_und_map(n, P, k, off, ctypes.byref(u), ctypes.byref(v))
                     assert (u.value, v.value) == want
                 k += 1
+
+
+def test_row_bounds_without_wide_division(sh):
+    """r_c = floor(c n / P) through n = qP + r and an invariant multiplier."""
+    import ctypes as C
+    sh.sh_row_bound.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64]
+    sh.sh_row_bound.restype = C.c_uint64
+    rng = np.random.default_rng(9)
+    for n, P in [(1 << 36, 1 << 16), (65536, 64), (12345, 31), (10, 3), (2 ** 63 + 11, 1 << 24),
+                 (2 ** 64 - 1, 3), (7, 7), (1 << 20, 32)]:
+        cs = set(range(0, min(P, 50) + 1)) | {P} | {int(x) for x in rng.integers(0, P + 1, 200)}
+        for c in cs:
+            assert sh.sh_row_bound(n, P, c) == c * n // P, (n, P, c)
