@@ -66,6 +66,8 @@ static __global__ void chunk_tree_band(RowBounds rb, uint64_t seed, uint64_t m, 
 }
 
 // ---------------------------------------------------------------- tile tree
+constexpr uint64_t SMALL_FAIR_BITS = 4096;  // fair-bit counts up to this size stay on one lane
+
 // One level of the tile trees of chunks [c_begin, c_begin + C): node (c, j) at
 // `level` with count in[c 2^level + j] splits its universe at the middle tile
 // boundary; out[2 (c 2^level + j)] gets X, out[... + 1] the rest.
@@ -107,10 +109,15 @@ __global__ void __launch_bounds__(256)
           uint64_t r = 0;
           st = hyper_general(hp, s, r);
           X = st ? 0 : hyper_finish(hp, r);
+        } else if (hp.t1 <= SMALL_FAIR_BITS) {
+          // a short fair-bit count runs on its own lane
+          Stream s(seed, sid, TAG_TILE);
+          X = hyper_finish(hp, popcount_bits(hp.t1, s));
         }
       }
     }
-    unsigned todo = __ballot_sync(0xffffffffu, live && st == ST_OK && hp.kind == 1);
+    unsigned todo = __ballot_sync(0xffffffffu, live && st == ST_OK && hp.kind == 1 &&
+                                                   hp.t1 > SMALL_FAIR_BITS);
     while (todo) {
       const int src = __ffs(todo) - 1;
       todo &= todo - 1;

@@ -65,25 +65,67 @@ __device__ __forceinline__ uint32_t bucket_of(uint64_t v, uint64_t nbmul, uint32
   return q < nb ? uint32_t(q) : nb - 1;
 }
 
+// Per-tile parameters, computed for all tiles at once by tile_desc_kernel so
+// that the leaf blocks start without a serial section.  k == 0 marks a tile
+// the leaf kernel skips (empty, or over k_max and handed to the re-split kernel).
+template <class Geom>
+struct TileDesc {
+  uint64_t lo, L, base, node, nbmul;
+  uint32_t k, nb;
+  typename Geom::Ctx gx;
+};
+
+template <class Geom>
+__global__ void __launch_bounds__(256)
+    tile_desc_kernel(Geom g, uint64_t c_begin, int d, uint32_t k_max,
+                     const uint64_t* __restrict__ tile_cnt, const uint64_t* __restrict__ tile_off,
+                     uint64_t ntiles, TileDesc<Geom>* __restrict__ desc, unsigned long long* big,
+                     unsigned long long* nbig, int* err) {
+  for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < ntiles;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    TileDesc<Geom> td;
+    td.k = 0;
+    const uint64_t k = tile_cnt[t];
+    if (k > k_max) {
+      big[atomicAdd(nbig, 1ull)] = t;
+    } else if (k > 0) {
+      const uint64_t c = c_begin + (t >> d);
+      const uint64_t tau = t & ((uint64_t(1) << d) - 1);
+      const uint64_t U = g.universe(c);
+      const uint64_t W = tile_width(U, d);
+      td.lo = node_bound(U, W, d, d, tau);
+      td.L = node_bound(U, W, d, d, u128(tau) + 1) - td.lo;
+      if (k > td.L) {
+        set_error(err, ST_INTERNAL);
+      } else {
+        td.k = uint32_t(k);
+        td.base = tile_off[t];
+        td.node = (g.chunk_id(c) << 32) | ((uint64_t(1) << d) + tau);
+        uint32_t nb = 32;
+        while (nb < k) nb <<= 1;
+        td.nb = nb;
+        // bucket multiplier floor(2^64 nb / L) (0 means: bucket = value)
+        td.nbmul = (td.L <= nb) ? 0 : uint64_t(double(nb) * 0x1p64 / double(td.L));
+        td.gx = g.ctx(c);
+      }
+    }
+    desc[t] = td;
+  }
+}
+
 struct FastSmem {
   uint64_t A[K_MAX];          // draws scattered by bucket; later draw order / result
   uint64_t B[K_MAX];          // sorted draws; with DIGEST the rows u afterwards
-  uint16_t hist[K_MAX + 1];   // bucket counts -> starts; first_pos in the rare path
+  uint16_t hist[K_MAX + 2];   // bucket counts -> starts; first_pos in the rare path
   uint32_t bitT[K_MAX / 32], bitJ[K_MAX / 32];
-  // tile parameters, computed by thread 0
-  uint64_t lo, L, base, node, nbmul;
-  uint32_t k, nb;
-  int skip;
 };
 
 template <class Geom, class Sink, bool DIGEST>
 __global__ void __launch_bounds__(FAST_THREADS, 6)
-    leaf_fast_kernel(Geom g, Sink sink, uint64_t c_begin, int d, uint32_t k_max, uint64_t seed,
-                     RoundKeys rk, const uint64_t* __restrict__ tile_cnt,
-                     const uint64_t* __restrict__ tile_off, uint64_t ntiles, int* err,
-                     DigestOut dig, unsigned long long* big, unsigned long long* nbig) {
+    leaf_fast_kernel(Geom g, Sink sink, int d, uint64_t seed, RoundKeys rk,
+                     const TileDesc<Geom>* __restrict__ desc, uint64_t ntiles, int* err,
+                     DigestOut dig) {
   __shared__ FastSmem sm;
-  __shared__ typename Geom::Ctx s_gx;
   __shared__ unsigned bh[65];
   __shared__ unsigned long long red_d[FAST_THREADS / 32];
   __shared__ unsigned red_c1[FAST_THREADS / 32], red_nr[FAST_THREADS / 32];
@@ -91,50 +133,14 @@ __global__ void __launch_bounds__(FAST_THREADS, 6)
   __shared__ uint32_t s_fl, s_ll;
   const int tid = threadIdx.x;
 
+  for (uint32_t b = tid; b < (K_MAX + 2) / 2; b += FAST_THREADS)
+    reinterpret_cast<unsigned*>(sm.hist)[b] = 0;
+  __syncthreads();
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    // ---- tile parameters
-    if (tid == 0) {
-      const uint64_t k = tile_cnt[t];
-      sm.skip = 0;
-      if (k == 0) {
-        sm.skip = 1;
-      } else if (k > k_max) {
-        big[atomicAdd(nbig, 1ull)] = t;
-        sm.skip = 1;
-      } else {
-        const uint64_t c = c_begin + (t >> d);
-        const uint64_t tau = t & ((uint64_t(1) << d) - 1);
-        const uint64_t U = g.universe(c);
-        const uint64_t W = tile_width(U, d);
-        const uint64_t lo = node_bound(U, W, d, d, tau);
-        const uint64_t hi = node_bound(U, W, d, d, u128(tau) + 1);
-        if (k > hi - lo) {
-          set_error(err, ST_INTERNAL);
-          sm.skip = 1;
-        } else {
-          sm.k = uint32_t(k);
-          sm.lo = lo;
-          sm.L = hi - lo;
-          sm.base = tile_off[t];
-          sm.node = (g.chunk_id(c) << 32) | ((uint64_t(1) << d) + tau);
-          s_gx = g.ctx(c);
-          uint32_t nb = 32;
-          while (nb < k) nb <<= 1;
-          sm.nb = nb;
-          // bucket multiplier floor(2^64 nb / L) from FP64 (0 means: bucket = x)
-          sm.nbmul = (sm.L <= nb) ? 0 : uint64_t(double(nb) * 0x1p64 / double(sm.L));
-        }
-      }
-    }
-    __syncthreads();
-    if (sm.skip) {
-      __syncthreads();
-      continue;
-    }
-    const uint32_t k = sm.k, nb = sm.nb;
-    const uint64_t L = sm.L, Lk = L - k, node = sm.node, nbmul = sm.nbmul;
-    for (uint32_t b = tid; b <= nb; b += FAST_THREADS) sm.hist[b] = 0;
-    __syncthreads();
+    const TileDesc<Geom> td = desc[t];
+    if (td.k == 0) continue;  // uniform over the block
+    const uint32_t k = td.k, nb = td.nb;
+    const uint64_t L = td.L, Lk = L - k, node = td.node, nbmul = td.nbmul;
 
     // ---- 1./2. draws in registers, bucket counts and slots
     uint64_t x[2 * FAST_PAIRS];
@@ -286,8 +292,8 @@ __global__ void __launch_bounds__(FAST_THREADS, 6)
     }
     // ---- 6. emit
     unsigned long long dsum = 0;
-    const uint64_t lo = sm.lo, base = sm.base;
-    const typename Geom::Ctx gx = s_gx;
+    const uint64_t lo = td.lo, base = td.base;
+    const typename Geom::Ctx gx = td.gx;
     for (uint32_t r = tid; r < k; r += FAST_THREADS) {
       uint64_t u, v;
       g.map(gx, lo + res[r], u, v);
@@ -369,6 +375,10 @@ __global__ void __launch_bounds__(FAST_THREADS, 6)
       for (int b = tid; b < 65; b += FAST_THREADS)
         if (bh[b]) atomicAdd(&dig.hist[cl * 65 + b], (unsigned long long)bh[b]);
     }
+    // clear the bucket counters for the next tile (all of them: the rare path
+    // reuses the array)
+    for (uint32_t b = tid; b < (K_MAX + 2) / 2; b += FAST_THREADS)
+      reinterpret_cast<unsigned*>(sm.hist)[b] = 0;
     __syncthreads();
   }
 }
