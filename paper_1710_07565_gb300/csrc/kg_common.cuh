@@ -11,6 +11,9 @@ namespace kg {
 
 constexpr int K_LEAF = 1024;  // expected samples per tile (base-case threshold)
 constexpr int K_MAX = 2048;   // a leaf with more samples is split once more
+// leaf buckets are the next power of two >= k, so bucket arrays sized K_MAX
+// hold every bucket index only when K_MAX itself is a power of two
+static_assert((K_MAX & (K_MAX - 1)) == 0, "K_MAX must be a power of two");
 constexpr int LEAF_THREADS = 256;
 
 __device__ __forceinline__ void set_error(int* err, int code) {

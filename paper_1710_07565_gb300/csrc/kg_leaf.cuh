@@ -18,7 +18,7 @@
 
 namespace kg {
 
-constexpr int FAST_THREADS = 128;
+constexpr int FAST_THREADS = 256;
 constexpr int FAST_PAIRS = K_MAX / (2 * FAST_THREADS);  // draw pairs per thread at k_max
 
 // Philox round keys of one seed: key + r * Weyl constant, r = 0..9.
@@ -114,14 +114,14 @@ __global__ void __launch_bounds__(256)
 }
 
 struct FastSmem {
-  uint64_t A[K_MAX];          // draws scattered by bucket; later draw order / result
-  uint64_t B[K_MAX];          // sorted draws; with DIGEST the rows u afterwards
-  uint16_t hist[K_MAX + 2];   // bucket counts -> starts; first_pos in the rare path
+  uint64_t A[K_MAX];          // draws scattered by bucket, then sorted in place;
+                              // with DIGEST the rows u afterwards
+  uint16_t hist[K_MAX + 2];   // bucket counts -> starts; per-draw codes in the rare path
   uint32_t bitT[K_MAX / 32], bitJ[K_MAX / 32];
 };
 
 template <class Geom, class Sink, bool DIGEST>
-__global__ void __launch_bounds__(FAST_THREADS, 6)
+__global__ void __launch_bounds__(FAST_THREADS, 5)
     leaf_fast_kernel(Geom g, Sink sink, int d, uint64_t seed, RoundKeys rk,
                      const TileDesc<Geom>* __restrict__ desc, uint64_t ntiles, int* err,
                      DigestOut dig) {
@@ -208,12 +208,15 @@ __global__ void __launch_bounds__(FAST_THREADS, 6)
           const uint32_t b = slot[2 * s + h] & 0xffffu;
           const uint32_t p = sm.hist[b] + (slot[2 * s + h] >> 16);
           sm.A[p] = x[2 * s + h];
-          slot[2 * s + h] = p;  // now the scatter position
+          slot[2 * s + h] = b | (p << 16);  // bucket and scatter position
         }
     }
     __syncthreads();
-    // ---- 4. rank inside the bucket (ties by scatter position)
+    // ---- 4. rank inside the bucket (ties by scatter position); the rank lies
+    // in the bucket's own slot range, so after a barrier the values are
+    // written back in place
     int dup = 0;
+    uint32_t rank[2 * FAST_PAIRS];
 #pragma unroll
     for (int s = 0; s < FAST_PAIRS; ++s) {
       const uint32_t i = 2 * (tid + FAST_THREADS * s);
@@ -222,8 +225,8 @@ __global__ void __launch_bounds__(FAST_THREADS, 6)
       for (int h = 0; h < 2; ++h)
         if (i + h < k) {
           const uint64_t v = x[2 * s + h];
-          const uint32_t p = slot[2 * s + h];
-          const uint32_t b = bucket_of(v, nbmul, nb);
+          const uint32_t p = slot[2 * s + h] >> 16;
+          const uint32_t b = slot[2 * s + h] & 0xffffu;
           const uint32_t s0 = sm.hist[b], s1 = sm.hist[b + 1];
           uint32_t r = s0;
           for (uint32_t q = s0; q < s1; ++q) {
@@ -231,13 +234,26 @@ __global__ void __launch_bounds__(FAST_THREADS, 6)
             r += (y < v) || (y == v && q < p);
             dup |= (y == v && q != p);
           }
-          sm.B[r] = v;
+          rank[2 * s + h] = r;
         }
     }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < FAST_PAIRS; ++s) {
+      const uint32_t i = 2 * (tid + FAST_THREADS * s);
+      if (i >= k) break;
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+        if (i + h < k) sm.A[rank[2 * s + h]] = x[2 * s + h];
+    }
     const int any_dup = __syncthreads_or(dup);
-    uint64_t* res = sm.B;
+    uint64_t* res = sm.A;
     if (any_dup) {
-      // ---- 5. sequential resolution in draw order (see leaf_sample_emit)
+      // ---- 5. sequential resolution in draw order.  A value v < L-k can only
+      // be taken by an earlier draw of v itself (first occurrence wins); the
+      // values L-k .. L-1 are tracked in a bitmap because replacements land
+      // there.  Per draw a 16-bit code: the first sorted position of v, or
+      // 0x8000 | (v - (L-k)) for the top k values.
 #pragma unroll
       for (int s = 0; s < FAST_PAIRS; ++s) {
         const uint32_t i = 2 * (tid + FAST_THREADS * s);
@@ -246,49 +262,61 @@ __global__ void __launch_bounds__(FAST_THREADS, 6)
         for (int h = 0; h < 2; ++h)
           if (i + h < k) {
             const uint64_t v = x[2 * s + h];
-            sm.A[i + h] = v;
-            uint32_t a = 0, e = k;
-            while (a < e) {
-              const uint32_t mid = (a + e) >> 1;
-              if (sm.B[mid] < v)
-                a = mid + 1;
-              else
-                e = mid;
+            uint16_t code;
+            if (v >= Lk) {
+              code = uint16_t(0x8000u | uint32_t(v - Lk));
+            } else {
+              uint32_t a = 0, e = k;
+              while (a < e) {
+                const uint32_t mid = (a + e) >> 1;
+                if (sm.A[mid] < v)
+                  a = mid + 1;
+                else
+                  e = mid;
+              }
+              code = uint16_t(a);
             }
-            sm.hist[i + h] = uint16_t(a);
+            sm.hist[i + h] = code;
           }
       }
       for (uint32_t w = tid; w < K_MAX / 32; w += FAST_THREADS) sm.bitT[w] = sm.bitJ[w] = 0;
       __syncthreads();
       if (tid == 0) {
         for (uint32_t i = 0; i < k; ++i) {
-          const uint64_t v = sm.A[i];
-          if (v < Lk) {
-            const uint32_t fp = sm.hist[i];
+          const uint32_t code = sm.hist[i];
+          if (!(code & 0x8000u)) {
+            const uint32_t fp = code;
             if (sm.bitT[fp >> 5] & (1u << (fp & 31)))
               sm.bitJ[i >> 5] |= 1u << (i & 31);
             else
               sm.bitT[fp >> 5] |= 1u << (fp & 31);
           } else {
-            const uint32_t bj = uint32_t(v - Lk);
+            const uint32_t bj = code & 0x7fffu;
             if (sm.bitJ[bj >> 5] & (1u << (bj & 31)))
               sm.bitJ[i >> 5] |= 1u << (i & 31);
             else
               sm.bitJ[bj >> 5] |= 1u << (bj & 31);
           }
         }
+        // the taken set in increasing order, compacted in place (the write
+        // index never passes the read index)
         uint32_t o = 0;
+        uint64_t prev = 0;
         for (uint32_t r = 0; r < k; ++r) {
-          const uint64_t v = sm.B[r];
+          const uint64_t v = sm.A[r];
           if (v >= Lk) break;
-          if ((r == 0 || sm.B[r - 1] != v) && (sm.bitT[r >> 5] & (1u << (r & 31)))) sm.A[o++] = v;
+          const bool first = (r == 0 || prev != v);
+          prev = v;
+          if (first && (sm.bitT[r >> 5] & (1u << (r & 31)))) sm.A[o++] = v;
         }
         for (uint32_t bj = 0; bj < k; ++bj)
-          if (sm.bitJ[bj >> 5] & (1u << (bj & 31))) sm.A[o++] = Lk + bj;
+          if (sm.bitJ[bj >> 5] & (1u << (bj & 31))) {
+            if (o < k) sm.A[o] = Lk + bj;
+            ++o;
+          }
         if (o != k) set_error(err, ST_INTERNAL);
       }
       __syncthreads();
-      res = sm.A;
     }
     // ---- 6. emit
     unsigned long long dsum = 0;
