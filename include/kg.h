@@ -164,6 +164,39 @@ kg_status kg_gnm_directed_noalloc(uint64_t n, uint64_t m, uint64_t seed, uint32_
                                   int id_bytes, void* d_out, uint64_t cap_edges, int* d_status,
                                   void* stream);
 
+/*
+ * Batched G(n,m): many independent instances generated together (the paper
+ * runs one instance on many PEs; batching runs many instances on one GPU).
+ * kg_batch_create validates the instances, lays out their outputs one after
+ * another in instance order, allocates the plan's device memory and uploads
+ * the instance table -- once (it synchronises).  kg_batch_run then only
+ * enqueues kernels on `stream`: no allocation, no host synchronisation, a
+ * fixed launch sequence, so it can be captured into a CUDA graph and
+ * replayed.  The output of instance i occupies entries
+ * [offsets[i], offsets[i+1]) of d_out (kg_batch_offsets) and is bit-identical
+ * to what kg_gnm_directed / kg_gnm_undirected write for the same instance
+ * (uint32 ids only: id_bytes must be 4).  Limits per instance: chunks <= 64
+ * (directed) or <= 32 (undirected), n <= 2^32, m <= 2^44.
+ * kg_batch_tune times the launch shapes that do not change the output
+ * (threads of the tree kernel, grid of the leaf kernel) on the caller's
+ * buffer and keeps the fastest.
+ */
+typedef struct kg_instance {
+  uint64_t n, m, seed;
+  uint32_t chunks;
+  int32_t undirected; /* 0: directed, 1: undirected */
+} kg_instance;
+typedef struct kg_batch kg_batch;
+kg_status kg_batch_create(const kg_instance* h_instances, uint32_t count, int id_bytes,
+                          kg_batch** out_batch);
+uint64_t kg_batch_entries(const kg_batch* batch);
+kg_status kg_batch_offsets(const kg_batch* batch, uint64_t* h_offsets /* count + 1 */);
+kg_status kg_batch_run(kg_batch* batch, void* d_out, uint64_t cap_entries, void* stream);
+kg_status kg_batch_tune(kg_batch* batch, void* d_out, uint64_t cap_entries, int reps, void* stream);
+kg_status kg_batch_get_tuning(const kg_batch* batch, uint32_t* tree_threads,
+                              uint32_t* leaf_grid_cap);
+kg_status kg_batch_destroy(kg_batch* batch);
+
 /* Order-independent digest of an edge list (see kg_gnm_directed_range):
  * *d_digest = sum of splitmix64(u xor rotl64(v, 32)) over `count` pairs. */
 kg_status kg_edge_digest(const void* d_edges, uint64_t count, int id_bytes, uint64_t* d_digest,

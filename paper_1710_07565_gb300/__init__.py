@@ -70,6 +70,20 @@ def lib() -> ctypes.CDLL:
                     continue
                 f.argtypes = args
                 f.restype = ctypes.c_int
+            L.kg_batch_create.argtypes = [vp, u32, i32, ctypes.POINTER(vp)]
+            L.kg_batch_create.restype = ctypes.c_int
+            L.kg_batch_entries.argtypes = [vp]
+            L.kg_batch_entries.restype = u64
+            L.kg_batch_offsets.argtypes = [vp, vp]
+            L.kg_batch_offsets.restype = ctypes.c_int
+            L.kg_batch_run.argtypes = [vp, vp, u64, vp]
+            L.kg_batch_run.restype = ctypes.c_int
+            L.kg_batch_tune.argtypes = [vp, vp, u64, i32, vp]
+            L.kg_batch_tune.restype = ctypes.c_int
+            L.kg_batch_get_tuning.argtypes = [vp, vp, vp]
+            L.kg_batch_get_tuning.restype = ctypes.c_int
+            L.kg_batch_destroy.argtypes = [vp]
+            L.kg_batch_destroy.restype = ctypes.c_int
             L.kg_status_str.argtypes = [ctypes.c_int]
             L.kg_status_str.restype = ctypes.c_char_p
             L.kg_launch_count.argtypes = []
@@ -184,6 +198,51 @@ def kg_profile_end():
     if st != KG_OK:
         raise KGError(st, "kg_profile_end")
     return {c: (ms[i], n[i]) for i, c in enumerate(PROF_CLASSES)}
+
+
+class kg_instance(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("m", ctypes.c_uint64), ("seed", ctypes.c_uint64),
+                ("chunks", ctypes.c_uint32), ("undirected", ctypes.c_int32)]
+
+
+def kg_batch_create(instances, id_bytes=4):
+    """instances: sequence of dicts with n, m, seed, chunks, undirected.  Returns a handle."""
+    arr = (kg_instance * max(len(instances), 1))()
+    for i, q in enumerate(instances):
+        arr[i] = kg_instance(q["n"], q["m"], q["seed"], q["chunks"], 1 if q["undirected"] else 0)
+    h = ctypes.c_void_p()
+    _call("kg_batch_create", ctypes.cast(arr, ctypes.c_void_p), len(instances), id_bytes,
+          ctypes.byref(h))
+    return h
+
+
+def kg_batch_entries(h) -> int:
+    return lib().kg_batch_entries(h)
+
+
+def kg_batch_offsets(h, count):
+    import numpy as np
+    off = np.zeros(count + 1, dtype=np.uint64)
+    _call("kg_batch_offsets", h, off.ctypes.data_as(ctypes.c_void_p))
+    return off
+
+
+def kg_batch_run(h, d_out, cap_entries, stream):
+    return _call("kg_batch_run", h, d_out, cap_entries, stream)
+
+
+def kg_batch_tune(h, d_out, cap_entries, reps, stream):
+    return _call("kg_batch_tune", h, d_out, cap_entries, reps, stream)
+
+
+def kg_batch_get_tuning(h):
+    a, b = ctypes.c_uint32(), ctypes.c_uint32()
+    _call("kg_batch_get_tuning", h, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def kg_batch_destroy(h):
+    return _call("kg_batch_destroy", h)
 
 
 # ---------------------------------------------------------------- torch helpers

@@ -1,0 +1,784 @@
+// Batched G(n,m): many independent instances (directed or undirected, each
+// with its own n, m, seed and chunk count) generated by one fixed sequence of
+// kernels over all instances.  kg_batch_create lays the instances out and
+// uploads their table once; kg_batch_run only enqueues device work (no
+// allocation, no host synchronisation), so the whole batch can be captured
+// into one CUDA graph and replayed.  The output is the concatenation, in
+// instance order, of what the per-instance entry points write.
+#include <algorithm>
+#include <vector>
+
+#include "../../include/kg.h"
+#include "kg_run.cuh"
+#include "kg_und.cuh"
+
+namespace kg {
+
+struct BInst {
+  uint64_t n, m, seed;
+  uint32_t P, undirected;
+  int d, D;
+  uint64_t C;
+  uint64_t chunk_base, tile_base, sample_base, pair_base, vert_base, out_base;
+  RowBounds rb;
+  DivU64 div;  // by n-1 (directed)
+};
+
+// Geometry context of one chunk of any instance.
+struct BatchCtx {
+  uint64_t nm1, r0, ri, rj, sj;
+  DivU64 div;
+  int kind;  // 0 directed, 1 undirected rectangle, 2 undirected triangle
+};
+
+struct BatchGeom {
+  using Ctx = BatchCtx;
+  __device__ __forceinline__ void map(const Ctx& x, uint64_t off, uint64_t& u, uint64_t& v) const {
+    if (x.kind == 0) {
+      const uint64_t q = div_q(x.div, off);
+      const uint64_t w = off - q * x.nm1;
+      u = x.r0 + q;
+      v = w + (w >= u ? 1 : 0);
+    } else if (x.kind == 1) {
+      const uint64_t q = off / x.sj;
+      u = x.ri + q;
+      v = x.rj + (off - q * x.sj);
+    } else {
+      uint64_t w = uint64_t((1.0 + sqrt(1.0 + 8.0 * double(off))) * 0.5);
+      if (w < 1) w = 1;
+      while (u128(w) * (w - 1) / 2 > off) --w;
+      while (u128(w + 1) * w / 2 <= off) ++w;
+      u = x.ri + w;
+      v = x.ri + (off - uint64_t(u128(w) * (w - 1) / 2));
+    }
+  }
+  __device__ __forceinline__ uint64_t rows(uint64_t) const { return 0; }
+};
+
+// Output positions below 2^62 go to the final output, those with bit 62 set
+// to the undirected pair scratch.
+constexpr uint64_t SCRATCH_BIT = uint64_t(1) << 62;
+
+struct BatchSink {
+  uint32_t* out;
+  uint32_t* scratch;
+  uint64_t cap_out, cap_scratch;
+  int* err;
+  __device__ __forceinline__ void write(uint64_t pos, uint64_t u, uint64_t v) const {
+    uint32_t* dst = out;
+    uint64_t cap = cap_out;
+    if (pos & SCRATCH_BIT) {
+      pos &= ~SCRATCH_BIT;
+      dst = scratch;
+      cap = cap_scratch;
+    }
+    if (pos >= cap) {
+      set_error(err, ST_CAPACITY);
+      return;
+    }
+    uint2 w;
+    w.x = uint32_t(u);
+    w.y = uint32_t(v);
+    reinterpret_cast<uint2*>(dst)[pos] = w;
+  }
+  __device__ __forceinline__ uint64_t read_u(uint64_t pos) const {
+    const uint32_t* src = (pos & SCRATCH_BIT) ? scratch : out;
+    return src[2 * (pos & ~SCRATCH_BIT)];
+  }
+};
+
+// index i with base[i] <= x < base[i+1] (base non-decreasing, base[count] = total)
+__device__ __forceinline__ uint32_t find_inst(const BInst* __restrict__ inst, uint32_t count,
+                                              uint64_t x, int which) {
+  uint32_t a = 0, b = count;
+  while (b - a > 1) {
+    const uint32_t mid = (a + b) >> 1;
+    const uint64_t v = which == 0 ? inst[mid].tile_base
+                       : which == 1 ? inst[mid].pair_base
+                                    : inst[mid].vert_base;
+    if (v <= x)
+      a = mid;
+    else
+      b = mid;
+  }
+  return a;
+}
+
+__device__ __forceinline__ uint64_t b_universe(const BInst& I, uint64_t c) {
+  if (!I.undirected) return (I.rb(c + 1) - I.rb(c)) * (I.n - 1);
+  uint32_t i, j;
+  UndGeom::ij(c, i, j);
+  const uint64_t si = I.rb(uint64_t(i) + 1) - I.rb(i);
+  if (i == j) return si ? uint64_t(u128(si) * (si - 1) / 2) : 0;
+  return si * (I.rb(uint64_t(j) + 1) - I.rb(j));
+}
+
+__device__ __forceinline__ uint64_t b_chunk_id(const BInst& I, uint64_t c) {
+  if (!I.undirected) return c;
+  uint32_t i, j;
+  UndGeom::ij(c, i, j);
+  return uint64_t(i) * I.P + j;
+}
+
+// ---------------------------------------------------------------- trees
+// One block per instance: the chunk split tree (directed) or quadrant tree
+// (undirected), then the instance's tile tree level by level.
+constexpr int BT_MAXC = 32 * 33 / 2;  // undirected chunks at P <= 32
+
+__global__ void __launch_bounds__(256)
+    batch_trees(const BInst* __restrict__ inst, uint64_t* __restrict__ chunk_cnt,
+                uint64_t* __restrict__ tmp, uint64_t* __restrict__ tile_cnt, int* err) {
+  __shared__ uint64_t node_cnt[128];
+  __shared__ QNode ql[2][BT_MAXC];
+  __shared__ uint32_t qn[2];
+  const BInst I = inst[blockIdx.x];
+  const int tid = threadIdx.x;
+  uint64_t* cc = chunk_cnt + I.chunk_base;
+  if (!I.undirected) {
+    if (tid == 0) node_cnt[1] = I.m;
+    __syncthreads();
+    for (int level = 0; level <= I.D; ++level) {
+      for (uint64_t j = tid; j < (uint64_t(1) << level); j += blockDim.x) {
+        const uint64_t h = (uint64_t(1) << level) + j;
+        uint32_t a, b;
+        if (!chunk_range(I.P, h, level, a, b)) continue;
+        const uint64_t mc = node_cnt[h];
+        if (b - a == 1) {
+          cc[a] = mc;
+          continue;
+        }
+        const uint32_t s = a + (b - a + 1) / 2;
+        const uint64_t ra = I.rb(a);
+        const u128 N = u128(I.rb(b) - ra) * (I.n - 1);
+        const u128 NL = u128(I.rb(s) - ra) * (I.n - 1);
+        Stream st(I.seed, h, TAG_CHUNK_TREE);
+        uint64_t X = 0;
+        const int e = hypergeometric(N, NL, mc, st, X);
+        if (e) {
+          set_error(err, e);
+          X = 0;
+        }
+        node_cnt[2 * h] = X;
+        node_cnt[2 * h + 1] = mc - X;
+      }
+      __syncthreads();
+    }
+  } else {
+    if (tid == 0) {
+      ql[0][0] = QNode{0, I.P, 0, I.P, I.m};
+      qn[0] = 1;
+      qn[1] = 0;
+    }
+    __syncthreads();
+    for (int level = 0; level <= I.D; ++level) {
+      const int cur = level & 1, nxt = cur ^ 1;
+      const uint32_t count = qn[cur];
+      for (uint32_t idx = tid; idx < count; idx += blockDim.x) {
+        const QNode q = ql[cur][idx];
+        const bool tri = (q.a == q.c && q.b == q.d);
+        if ((tri && q.b - q.a == 1) || (!tri && q.b - q.a == 1 && q.d - q.c == 1)) {
+          cc[und_chunk_index(q.a, q.c)] = q.cnt;
+          continue;
+        }
+        Stream st(I.seed, quad_id(q.a, q.b, q.c, q.d), TAG_QUAD);
+        QNode parts[4];
+        u128 size[4];
+        int np = 0;
+        if (tri) {
+          const uint32_t l = (q.b - q.a + 1) / 2;
+          const uint64_t ra = I.rb(q.a), rm = I.rb(q.a + l), rbb = I.rb(q.b);
+          const uint64_t S1 = rm - ra, S2 = rbb - rm;
+          parts[0] = QNode{q.a, q.a + l, q.a, q.a + l, 0};
+          parts[1] = QNode{q.a + l, q.b, q.a, q.a + l, 0};
+          parts[2] = QNode{q.a + l, q.b, q.a + l, q.b, 0};
+          size[0] = tri_pairs(S1);
+          size[1] = u128(S2) * S1;
+          size[2] = tri_pairs(S2);
+          np = 3;
+        } else {
+          uint32_t rlo[2] = {q.a, 0}, rhi[2] = {q.b, 0}, clo[2] = {q.c, 0}, chi[2] = {q.d, 0};
+          int nr = 1, nc = 1;
+          if (q.b - q.a >= 2) {
+            const uint32_t s = q.a + (q.b - q.a + 1) / 2;
+            rhi[0] = s;
+            rlo[1] = s;
+            rhi[1] = q.b;
+            nr = 2;
+          }
+          if (q.d - q.c >= 2) {
+            const uint32_t s = q.c + (q.d - q.c + 1) / 2;
+            chi[0] = s;
+            clo[1] = s;
+            chi[1] = q.d;
+            nc = 2;
+          }
+          for (int i = 0; i < nr; ++i)
+            for (int j = 0; j < nc; ++j) {
+              parts[np] = QNode{rlo[i], rhi[i], clo[j], chi[j], 0};
+              size[np] = u128(I.rb(rhi[i]) - I.rb(rlo[i])) * (I.rb(chi[j]) - I.rb(clo[j]));
+              ++np;
+            }
+        }
+        u128 N = 0;
+        for (int i = 0; i < np; ++i) N += size[i];
+        uint64_t rem = q.cnt;
+        for (int i = 0; i < np - 1; ++i) {
+          uint64_t X = 0;
+          const int e = hypergeometric(N, size[i], rem, st, X);
+          if (e) {
+            set_error(err, e);
+            X = 0;
+          }
+          parts[i].cnt = X;
+          N -= size[i];
+          rem -= X;
+        }
+        parts[np - 1].cnt = rem;
+        const uint32_t o = atomicAdd(&qn[nxt], uint32_t(np));
+        for (int i = 0; i < np; ++i)
+          if (o + i < BT_MAXC) ql[nxt][o + i] = parts[i];
+      }
+      __syncthreads();
+      if (tid == 0) qn[cur] = 0;
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  // tile tree: level l reads `in`, writes the next level; the last level lands in tile_cnt
+  const int d = I.d;
+  const uint64_t C = I.C;
+  uint64_t* out_last = tile_cnt + I.tile_base;
+  uint64_t* out_tmp = tmp + I.tile_base;
+  if (d == 0) {
+    for (uint64_t c = tid; c < C; c += blockDim.x) out_last[c] = cc[c];
+    return;
+  }
+  const uint64_t* in = cc;
+  for (int level = 0; level < d; ++level) {
+    uint64_t* out = ((d - 1 - level) & 1) ? out_tmp : out_last;
+    const uint64_t total = C << level;
+    for (uint64_t node = tid; node < total; node += blockDim.x) {
+      const uint64_t c = node >> level;
+      const uint64_t j = node & ((uint64_t(1) << level) - 1);
+      const uint64_t U = b_universe(I, c);
+      const uint64_t W = tile_width(U, d);
+      const uint64_t lo = node_bound(U, W, d, level, j);
+      const uint64_t hi = node_bound(U, W, d, level, u128(j) + 1);
+      const uint64_t mid = node_bound(U, W, d, level + 1, u128(2) * j + 1);
+      const uint64_t k = in[node];
+      uint64_t X = 0;
+      int e = ST_INTERNAL;
+      if (k <= hi - lo) {
+        Stream st(I.seed, (b_chunk_id(I, c) << 32) | ((uint64_t(1) << level) + j), TAG_TILE);
+        e = hypergeometric(u128(hi - lo), u128(mid - lo), k, st, X);
+      }
+      if (e) {
+        set_error(err, e);
+        X = 0;
+      }
+      out[2 * node] = X;
+      out[2 * node + 1] = k - X;
+    }
+    __syncthreads();
+    in = out;
+  }
+}
+
+// ---------------------------------------------------------------- tile descriptors
+__global__ void __launch_bounds__(256)
+    batch_desc(const BInst* __restrict__ inst, uint32_t count, uint64_t ntiles, uint32_t k_max,
+               const uint64_t* __restrict__ tile_cnt, const uint64_t* __restrict__ tile_off,
+               TileDesc<BatchCtx>* __restrict__ desc, unsigned long long* big,
+               unsigned long long* nbig, int* err) {
+  for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < ntiles;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t ii = find_inst(inst, count, t, 0);
+    const BInst I = inst[ii];
+    const uint64_t local = t - I.tile_base;
+    const uint64_t c = local >> I.d;
+    const uint64_t tau = local & ((uint64_t(1) << I.d) - 1);
+    TileDesc<BatchCtx> td;
+    desc_fill(td, b_universe(I, c), I.d, tau, tile_cnt[t], k_max, err);
+    const uint64_t local_pos = tile_off[t] - I.sample_base;
+    td.base = I.undirected ? (SCRATCH_BIT | (I.pair_base + local_pos)) : (I.out_base + local_pos);
+    td.cid = b_chunk_id(I, c);
+    td.seed = I.seed;
+    BatchCtx x;
+    x.nm1 = I.n - 1;
+    x.div = I.div;
+    if (!I.undirected) {
+      x.kind = 0;
+      x.r0 = I.rb(c);
+    } else {
+      uint32_t i, j;
+      UndGeom::ij(c, i, j);
+      x.kind = (i == j) ? 2 : 1;
+      x.ri = I.rb(i);
+      x.rj = I.rb(j);
+      x.sj = I.rb(uint64_t(j) + 1) - x.rj;
+    }
+    td.gx = x;
+    if (td.flags == 1) big[atomicAdd(nbig, 1ull)] = t;
+    desc[t] = td;
+  }
+}
+
+// ---------------------------------------------------------------- undirected assembly
+__global__ void batch_und_degree(const BInst* __restrict__ inst, uint32_t count, uint64_t npairs,
+                                 const uint32_t* __restrict__ pairs,
+                                 unsigned long long* __restrict__ deg) {
+  for (uint64_t p = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < npairs;
+       p += uint64_t(gridDim.x) * blockDim.x) {
+    const BInst& I = inst[find_inst(inst, count, p, 1)];
+    atomicAdd(&deg[I.vert_base + pairs[2 * p]], 1ull);
+    atomicAdd(&deg[I.vert_base + pairs[2 * p + 1]], 1ull);
+  }
+}
+
+// absolute output position of the first entry of every undirected row
+__global__ void batch_und_rowpos(const BInst* __restrict__ inst, uint32_t count, uint64_t nverts,
+                                 const uint64_t* __restrict__ rowptr,
+                                 unsigned long long* __restrict__ rowpos) {
+  for (uint64_t r = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < nverts;
+       r += uint64_t(gridDim.x) * blockDim.x) {
+    const BInst& I = inst[find_inst(inst, count, r, 2)];
+    rowpos[r] = rowptr[r] - rowptr[I.vert_base] + I.out_base;
+  }
+}
+
+__global__ void batch_und_scatter(const BInst* __restrict__ inst, uint32_t count, uint64_t npairs,
+                                  const uint32_t* __restrict__ pairs,
+                                  unsigned long long* __restrict__ cursor,
+                                  uint32_t* __restrict__ out, uint64_t cap, int* err) {
+  for (uint64_t p = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < npairs;
+       p += uint64_t(gridDim.x) * blockDim.x) {
+    const BInst& I = inst[find_inst(inst, count, p, 1)];
+    const uint32_t u = pairs[2 * p], v = pairs[2 * p + 1];
+    const uint64_t a = atomicAdd(&cursor[I.vert_base + u], 1ull);
+    const uint64_t b = atomicAdd(&cursor[I.vert_base + v], 1ull);
+    if (a < cap && b < cap) {
+      out[2 * a] = u;
+      out[2 * a + 1] = v;
+      out[2 * b] = v;
+      out[2 * b + 1] = u;
+    } else {
+      set_error(err, ST_CAPACITY);
+    }
+  }
+}
+
+// Rows of <= 32 entries sorted by one warp (bitonic across lanes); longer rows listed.
+__global__ void __launch_bounds__(256)
+    batch_und_sort_short(uint64_t nverts, const unsigned long long* __restrict__ rowpos,
+                         const unsigned long long* __restrict__ deg, uint32_t* __restrict__ out,
+                         uint64_t cap, unsigned long long* long_rows, unsigned long long* nlong) {
+  const unsigned lane = threadIdx.x & 31;
+  const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t r = warp; r < nverts; r += nwarps) {
+    const uint64_t b = rowpos[r], dg = deg[r];
+    if (dg == 0 || b + dg > cap) continue;
+    if (dg > 32) {
+      if (lane == 0) long_rows[atomicAdd(nlong, 1ull)] = r;
+      continue;
+    }
+    uint64_t x = lane < dg ? uint64_t(out[2 * (b + lane) + 1]) : ~uint64_t(0);
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+      for (int j = k >> 1; j > 0; j >>= 1) {
+        const uint64_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        const bool up = ((lane & k) == 0);
+        const bool lower = ((lane & j) == 0);
+        const uint64_t mn = x < y ? x : y, mx = x < y ? y : x;
+        x = (lower == up) ? mn : mx;
+      }
+    }
+    if (lane < dg) out[2 * (b + lane) + 1] = uint32_t(x);
+  }
+}
+
+__global__ void __launch_bounds__(256)
+    batch_und_sort_long(const unsigned long long* __restrict__ rowpos,
+                        const unsigned long long* __restrict__ deg, uint32_t* __restrict__ out,
+                        const unsigned long long* __restrict__ long_rows,
+                        const unsigned long long* __restrict__ nlong) {
+  __shared__ uint64_t sh[LONG_SMEM];
+  const unsigned long long nl = *nlong;
+  for (unsigned long long q = blockIdx.x; q < nl; q += gridDim.x) {
+    const uint64_t r = long_rows[q];
+    const uint64_t b = rowpos[r], n = deg[r];
+    uint64_t N = 1;
+    while (N < n) N <<= 1;
+    const bool in_smem = n <= LONG_SMEM;
+    if (in_smem)
+      for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) sh[i] = out[2 * (b + i) + 1];
+    __syncthreads();
+    auto get = [&](uint64_t i) -> uint64_t { return in_smem ? sh[i] : uint64_t(out[2 * (b + i) + 1]); };
+    auto put = [&](uint64_t i, uint64_t x) {
+      if (in_smem)
+        sh[i] = x;
+      else
+        out[2 * (b + i) + 1] = uint32_t(x);
+    };
+    for (uint64_t k = 2; k <= N; k <<= 1) {
+      for (uint64_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
+        const uint64_t blk = i / (k / 2), off = i % (k / 2);
+        const uint64_t lo = blk * k + off, hi = blk * k + k - 1 - off;
+        if (hi < n) {
+          const uint64_t x = get(lo), y = get(hi);
+          if (y < x) {
+            put(lo, y);
+            put(hi, x);
+          }
+        }
+      }
+      __syncthreads();
+      for (uint64_t j = k / 4; j >= 1; j >>= 1) {
+        for (uint64_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
+          const uint64_t blk = i / j, off = i % j;
+          const uint64_t lo = blk * 2 * j + off, hi = lo + j;
+          if (hi < n) {
+            const uint64_t x = get(lo), y = get(hi);
+            if (y < x) {
+              put(lo, y);
+              put(hi, x);
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    if (in_smem)
+      for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) out[2 * (b + i) + 1] = uint32_t(sh[i]);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- the plan
+struct BatchPlan {
+  int device;
+  uint32_t count;
+  uint64_t tiles, chunks, pairs, verts, entries, samples;
+  int has_und;
+  std::vector<uint64_t> out_offsets;  // count + 1
+  // device memory owned by the plan
+  BInst* inst;
+  uint64_t *chunk_cnt, *tile_tmp, *tile_cnt, *tile_off;
+  TileDesc<BatchCtx>* desc;
+  unsigned long long *big, *nbig;
+  uint32_t* pairs_buf;
+  unsigned long long *deg, *rowpos, *cursor, *long_rows, *nlong;
+  uint64_t* rowptr;
+  void* arena;
+  size_t arena_bytes;
+  // launch shapes chosen by kg_batch_tune (they do not change the output)
+  unsigned tree_threads = 256;
+  unsigned leaf_grid_cap = 0x7fffffffu;
+  std::vector<void*> allocs;
+};
+
+static uint64_t piece(uint64_t b) { return (b + 255) & ~uint64_t(255); }
+static uint64_t scan_scratch(uint64_t n) {
+  const uint64_t items = 512 * 8, nb = (n + items - 1) / items;
+  if (n == 0 || nb == 1) return 0;
+  return piece(nb * 8) + piece((nb + 1) * 8) + scan_scratch(nb);
+}
+
+static int plan_alloc(BatchPlan* bp, void** p, uint64_t bytes) {
+  if (cudaMalloc(p, bytes ? bytes : 8) != cudaSuccess) return ST_CUDA;
+  bp->allocs.push_back(*p);
+  return ST_OK;
+}
+
+static void plan_free(BatchPlan* bp) {
+  for (void* p : bp->allocs) cudaFree(p);
+  bp->allocs.clear();
+}
+
+static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream_t s) {
+  int* err = device_error_word();
+  if (!err) return ST_CUDA;
+  const uint32_t count = bp->count;
+  Workspace ws(s, bp->arena, bp->arena_bytes);
+  {
+    ProfScope ps(PROF_CHUNK_TREE, s);
+    batch_trees<<<count, bp->tree_threads, 0, s>>>(bp->inst, bp->chunk_cnt, bp->tile_tmp,
+                                                   bp->tile_cnt, err);
+    if (launch_ok()) return ST_CUDA;
+  }
+  int st = scan_exclusive_u64(bp->tile_cnt, bp->tile_off, bp->tiles, ws, s);
+  if (st) return st;
+  if (cudaMemsetAsync(bp->nbig, 0, 8, s) != cudaSuccess) return ST_CUDA;
+  {
+    ProfScope ps(PROF_OTHER, s);
+    batch_desc<<<grid_for(bp->tiles, 256, 152 * 32), 256, 0, s>>>(
+        bp->inst, count, bp->tiles, K_MAX, bp->tile_cnt, bp->tile_off, bp->desc, bp->big,
+        bp->nbig, err);
+    if (launch_ok()) return ST_CUDA;
+  }
+  BatchSink sink{out, bp->pairs_buf, cap, bp->pairs, err};
+  const uint64_t gcap = bp->tiles < bp->leaf_grid_cap ? bp->tiles : bp->leaf_grid_cap;
+  {
+    ProfScope ps(PROF_LEAF, s);
+    leaf_fast_kernel<BatchGeom, BatchSink, false, true><<<unsigned(gcap ? gcap : 1), FAST_THREADS, 0, s>>>(
+        BatchGeom{}, sink, 0, RoundKeys{}, bp->desc, bp->tiles, err,
+        DigestOut{nullptr, nullptr, nullptr});
+    if (launch_ok()) return ST_CUDA;
+  }
+  {
+    ProfScope ps(PROF_OTHER, s);
+    leaf_resplit_kernel<BatchGeom, BatchSink, false, TileDesc<BatchCtx>><<<152, LEAF_THREADS, 0, s>>>(
+        BatchGeom{}, sink, K_MAX, bp->desc, err, DigestOut{nullptr, nullptr, nullptr}, bp->big,
+        bp->nbig);
+    if (launch_ok()) return ST_CUDA;
+  }
+  if (!bp->has_und) return ST_OK;
+  const uint64_t V = bp->verts, Mp = bp->pairs;
+  if (cudaMemsetAsync(bp->deg, 0, V * 8, s) != cudaSuccess ||
+      cudaMemsetAsync(bp->nlong, 0, 8, s) != cudaSuccess)
+    return ST_CUDA;
+  {
+    ProfScope ps(PROF_ASSEMBLY, s);
+    batch_und_degree<<<grid_for(Mp, 256, 152 * 32), 256, 0, s>>>(bp->inst, count, Mp,
+                                                                 bp->pairs_buf, bp->deg);
+    if (launch_ok()) return ST_CUDA;
+  }
+  st = scan_exclusive_u64(reinterpret_cast<const uint64_t*>(bp->deg), bp->rowptr, V, ws, s);
+  if (st) return st;
+  {
+    ProfScope ps(PROF_ASSEMBLY, s);
+    batch_und_rowpos<<<grid_for(V, 256, 152 * 32), 256, 0, s>>>(bp->inst, count, V, bp->rowptr,
+                                                                bp->rowpos);
+    if (launch_ok()) return ST_CUDA;
+  }
+  if (cudaMemcpyAsync(bp->cursor, bp->rowpos, V * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    return ST_CUDA;
+  {
+    ProfScope ps(PROF_ASSEMBLY, s);
+    batch_und_scatter<<<grid_for(Mp, 256, 152 * 32), 256, 0, s>>>(bp->inst, count, Mp,
+                                                                  bp->pairs_buf, bp->cursor, out,
+                                                                  cap, err);
+    if (launch_ok()) return ST_CUDA;
+  }
+  {
+    ProfScope ps(PROF_ASSEMBLY, s);
+    batch_und_sort_short<<<grid_for(V, 8, 152 * 32), 256, 0, s>>>(V, bp->rowpos, bp->deg, out, cap,
+                                                                  bp->long_rows, bp->nlong);
+    if (launch_ok()) return ST_CUDA;
+  }
+  ProfScope ps(PROF_ASSEMBLY, s);
+  batch_und_sort_long<<<152 * 2, 256, 0, s>>>(bp->rowpos, bp->deg, out, bp->long_rows, bp->nlong);
+  return launch_ok();
+}
+
+}  // namespace kg
+
+using namespace kg;
+
+struct kg_batch {
+  BatchPlan plan;
+};
+
+extern "C" {
+
+kg_status kg_batch_create(const kg_instance* h_inst, uint32_t count, int id_bytes,
+                          kg_batch** out_batch) {
+  if (!out_batch || (count && !h_inst) || id_bytes != 4) return KG_ERR_ARG;
+  *out_batch = nullptr;
+  std::vector<BInst> tab(count);
+  kg_batch* b = new kg_batch();
+  BatchPlan& bp = b->plan;
+  bp.count = count;
+  bp.out_offsets.assign(count + 1, 0);
+  uint64_t chunks = 0, tiles = 0, samples = 0, pairs = 0, verts = 0, entries = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    const kg_instance& q = h_inst[i];
+    BInst& I = tab[i];
+    I.n = q.n;
+    I.m = q.m;
+    I.seed = q.seed;
+    I.P = q.chunks;
+    I.undirected = q.undirected ? 1 : 0;
+    const uint32_t Pmax = I.undirected ? 32u : 64u;
+    if (q.n == 0 || q.chunks == 0 || q.chunks > q.n || q.chunks > Pmax || q.n > (uint64_t(1) << 32)) {
+      delete b;
+      return KG_ERR_ARG;
+    }
+    const u128 Ntot = I.undirected ? tri_pairs(q.n) : u128(q.n) * (q.n - 1);
+    if (u128(q.m) > Ntot) {
+      delete b;
+      return KG_ERR_ARG;
+    }
+    if (q.m > M_MAX) {
+      delete b;
+      return KG_ERR_RANGE;
+    }
+    const u128 rmax = (u128(q.n) + q.chunks - 1) / q.chunks;
+    const u128 Unom = I.undirected ? rmax * rmax : rmax * (q.n - 1);
+    if (tile_depth(q.m, Unom, Ntot, K_LEAF, I.d)) {
+      delete b;
+      return KG_ERR_RANGE;
+    }
+    I.D = 0;
+    while ((uint64_t(1) << I.D) < q.chunks) ++I.D;
+    I.C = I.undirected ? uint64_t(q.chunks) * (q.chunks + 1) / 2 : q.chunks;
+    I.rb = RowBounds::make(q.n, q.chunks);
+    I.div = make_div(q.n > 1 ? q.n - 1 : 1);
+    I.chunk_base = chunks;
+    I.tile_base = tiles;
+    I.sample_base = samples;
+    I.pair_base = pairs;
+    I.vert_base = verts;
+    I.out_base = entries;
+    bp.out_offsets[i] = entries;
+    chunks += I.C;
+    tiles += I.C << I.d;
+    samples += q.m;
+    if (I.undirected) {
+      pairs += q.m;
+      verts += q.n;
+      entries += 2 * q.m;
+    } else {
+      entries += q.m;
+    }
+  }
+  bp.out_offsets[count] = entries;
+  bp.chunks = chunks;
+  bp.tiles = tiles;
+  bp.samples = samples;
+  bp.pairs = pairs;
+  bp.verts = verts;
+  bp.entries = entries;
+  bp.has_und = pairs > 0;
+  if (cudaGetDevice(&bp.device) != cudaSuccess) {
+    delete b;
+    return KG_ERR_CUDA;
+  }
+  // the plan's device memory, allocated once
+  void* p;
+  int st = ST_OK;
+  auto A = [&](void** dst, uint64_t bytes) {
+    if (!st) st = plan_alloc(&bp, dst, bytes);
+  };
+  A(&p, sizeof(BInst) * (count ? count : 1));
+  bp.inst = static_cast<BInst*>(p);
+  A(&p, chunks * 8);
+  bp.chunk_cnt = static_cast<uint64_t*>(p);
+  A(&p, tiles * 8);
+  bp.tile_tmp = static_cast<uint64_t*>(p);
+  A(&p, tiles * 8);
+  bp.tile_cnt = static_cast<uint64_t*>(p);
+  A(&p, (tiles + 1) * 8);
+  bp.tile_off = static_cast<uint64_t*>(p);
+  A(&p, tiles * sizeof(TileDesc<BatchCtx>));
+  bp.desc = static_cast<TileDesc<BatchCtx>*>(p);
+  A(&p, tiles * 8);
+  bp.big = static_cast<unsigned long long*>(p);
+  A(&p, 8);
+  bp.nbig = static_cast<unsigned long long*>(p);
+  A(&p, pairs * 8);
+  bp.pairs_buf = static_cast<uint32_t*>(p);
+  A(&p, verts * 8);
+  bp.deg = static_cast<unsigned long long*>(p);
+  A(&p, (verts + 1) * 8);
+  bp.rowptr = static_cast<uint64_t*>(p);
+  A(&p, verts * 8);
+  bp.rowpos = static_cast<unsigned long long*>(p);
+  A(&p, verts * 8);
+  bp.cursor = static_cast<unsigned long long*>(p);
+  A(&p, verts * 8);
+  bp.long_rows = static_cast<unsigned long long*>(p);
+  A(&p, 8);
+  bp.nlong = static_cast<unsigned long long*>(p);
+  bp.arena_bytes = scan_scratch(tiles) + scan_scratch(verts) + 512;  // both scans of one run
+  A(&bp.arena, bp.arena_bytes);
+  if (!st && cudaMemcpy(bp.inst, tab.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice) !=
+                 cudaSuccess)
+    st = ST_CUDA;
+  if (st) {
+    plan_free(&bp);
+    delete b;
+    return kg_status(st);
+  }
+  *out_batch = b;
+  return KG_OK;
+}
+
+kg_status kg_batch_destroy(kg_batch* b) {
+  if (!b) return KG_OK;
+  plan_free(&b->plan);
+  delete b;
+  return KG_OK;
+}
+
+uint64_t kg_batch_entries(const kg_batch* b) { return b ? b->plan.entries : 0; }
+
+kg_status kg_batch_offsets(const kg_batch* b, uint64_t* h_offsets) {
+  if (!b || !h_offsets) return KG_ERR_ARG;
+  std::copy(b->plan.out_offsets.begin(), b->plan.out_offsets.end(), h_offsets);
+  return KG_OK;
+}
+
+kg_status kg_batch_run(kg_batch* b, void* d_out, uint64_t cap_entries, void* stream) {
+  if (!b) return KG_ERR_ARG;
+  if (cap_entries < b->plan.entries) return KG_ERR_CAPACITY;
+  if (b->plan.count == 0 || b->plan.entries == 0) return KG_OK;
+  if (!d_out) return KG_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != b->plan.device) return KG_ERR_ARG;
+  return kg_status(batch_run_impl(&b->plan, static_cast<uint32_t*>(d_out), cap_entries,
+                                  static_cast<cudaStream_t>(stream)));
+}
+
+// Autotuning over launch shapes that do not change the output: threads per
+// block of the tree kernel and the grid of the leaf kernel (one block per
+// tile, or a persistent grid striding over the tiles).  Each candidate runs
+// `reps` times on `stream`; the fastest is kept in the plan.
+kg_status kg_batch_tune(kg_batch* b, void* d_out, uint64_t cap_entries, int reps, void* stream) {
+  if (!b || reps < 1) return KG_ERR_ARG;
+  if (cap_entries < b->plan.entries) return KG_ERR_CAPACITY;
+  if (b->plan.count == 0 || b->plan.entries == 0) return KG_OK;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const unsigned trees[] = {128, 256};
+  const unsigned grids[] = {0x7fffffffu, 152u * 5 * 8, 152u * 5 * 2};
+  float best = 1e30f;
+  unsigned bt = 256, bg = 0x7fffffffu;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KG_ERR_CUDA;
+  kg_status st = KG_OK;
+  for (unsigned tt : trees)
+    for (unsigned gg : grids) {
+      b->plan.tree_threads = tt;
+      b->plan.leaf_grid_cap = gg;
+      float total = 0.f;
+      for (int r = 0; r < reps && st == KG_OK; ++r) {
+        cudaEventRecord(e0, s);
+        st = kg_status(batch_run_impl(&b->plan, static_cast<uint32_t*>(d_out), cap_entries, s));
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) st = KG_ERR_CUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        total += ms;
+      }
+      if (st == KG_OK && total < best) {
+        best = total;
+        bt = tt;
+        bg = gg;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->plan.tree_threads = bt;
+  b->plan.leaf_grid_cap = bg;
+  return st;
+}
+
+kg_status kg_batch_get_tuning(const kg_batch* b, uint32_t* tree_threads, uint32_t* leaf_grid_cap) {
+  if (!b) return KG_ERR_ARG;
+  if (tree_threads) *tree_threads = b->plan.tree_threads;
+  if (leaf_grid_cap) *leaf_grid_cap = b->plan.leaf_grid_cap;
+  return KG_OK;
+}
+
+}  // extern "C"

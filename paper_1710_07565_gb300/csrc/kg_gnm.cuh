@@ -468,10 +468,10 @@ __global__ void chunk_run_merge(Geom g, uint64_t c_begin, uint64_t C, int d,
 // Tiles with more than k_max samples: split further (levels below d) by the
 // same hypergeometric rule, left to right, until every leaf holds at most
 // k_max samples; the leaves are emitted in order from the tile's offset.
-template <class Geom, class Sink, bool DIGEST>
+// Everything about the tile comes from its descriptor.
+template <class Geom, class Sink, bool DIGEST, class Desc>
 __global__ void __launch_bounds__(LEAF_THREADS)
-    leaf_resplit_kernel(Geom g, Sink sink, uint64_t c_begin, int d, uint32_t k_max, uint64_t seed,
-                        const uint64_t* __restrict__ tile_cnt, const uint64_t* __restrict__ tile_off,
+    leaf_resplit_kernel(Geom g, Sink sink, uint32_t k_max, const Desc* __restrict__ desc,
                         int* err, DigestOut dig, const unsigned long long* __restrict__ big,
                         const unsigned long long* __restrict__ nbig) {
   __shared__ LeafSmem sm;
@@ -483,7 +483,9 @@ __global__ void __launch_bounds__(LEAF_THREADS)
   const unsigned long long nb = *nbig;
   for (unsigned long long bi = blockIdx.x; bi < nb; bi += gridDim.x) {
     const uint64_t t = big[bi];
-    const uint64_t k = tile_cnt[t];
+    const Desc td = desc[t];
+    const uint64_t k = td.k;
+    const uint64_t seed = td.seed;
     unsigned long long dsum = 0;
     uint32_t c1 = 0, nr = 0;
     uint64_t fu = 0, lu = 0;
@@ -491,17 +493,13 @@ __global__ void __launch_bounds__(LEAF_THREADS)
     if (DIGEST) {
       for (int b = threadIdx.x; b < 65; b += LEAF_THREADS) bh[b] = 0;
     }
-    const uint64_t c = c_begin + (t >> d);
-    const uint64_t tau = t & ((uint64_t(1) << d) - 1);
-    const uint64_t U = g.universe(c);
-    const uint64_t W = tile_width(U, d);
-    const uint64_t cid = g.chunk_id(c);
-    const typename Geom::Ctx gx = g.ctx(c);
-    uint64_t base = tile_off[t];
+    const int d = td.d;
+    const uint64_t U = td.U, W = td.W, cid = td.cid;
+    uint64_t base = td.base;
     const uint64_t base0 = base;
     if (threadIdx.x == 0) {
       sm.stack_level[0] = d;
-      sm.stack_j[0] = tau;
+      sm.stack_j[0] = td.tau;
       sm.stack_k[0] = k;
       sm.sp = 1;
     }
@@ -565,7 +563,7 @@ __global__ void __launch_bounds__(LEAF_THREADS)
       const uint32_t kk = uint32_t(sm.leaf_k);
       const uint64_t lo = node_bound(U, W, d, lv, j);
       const uint64_t hi = node_bound(U, W, d, lv, u128(j) + 1);
-      leaf_sample_emit<Geom, Sink, DIGEST>(g, gx, sink, sm, seed,
+      leaf_sample_emit<Geom, Sink, DIGEST>(g, td.gx, sink, sm, seed,
                                            (cid << 32) | ((uint64_t(1) << lv) + j), lo, hi - lo,
                                            kk, base, err, dsum);
       base += kk;

@@ -65,50 +65,71 @@ __device__ __forceinline__ uint32_t bucket_of(uint64_t v, uint64_t nbmul, uint32
   return q < nb ? uint32_t(q) : nb - 1;
 }
 
-// Per-tile parameters, computed for all tiles at once by tile_desc_kernel so
-// that the leaf blocks start without a serial section.  k == 0 marks a tile
-// the leaf kernel skips (empty, or over k_max and handed to the re-split kernel).
-template <class Geom>
+// Per-tile parameters, computed for all tiles at once (tile_desc_kernel, or
+// the batched engine's descriptor kernel) so that the leaf blocks start
+// without a serial section.  flags: 0 = sample this tile, 1 = over k_max
+// (left to the re-split kernel), 2 = nothing to do.
+template <class Ctx>
 struct TileDesc {
-  uint64_t lo, L, base, node, nbmul;
-  uint32_t k, nb;
-  typename Geom::Ctx gx;
+  uint64_t lo, L, base, cid, nbmul, U, W, seed;
+  uint32_t k, nb, tau;
+  int d, flags;
+  Ctx gx;
+  __host__ __device__ __forceinline__ uint64_t node(int level, uint64_t j) const {
+    return (cid << 32) | ((uint64_t(1) << level) + j);
+  }
 };
+
+// Fills the tile fields from (U, d, tau, k); the caller sets base, cid, seed, gx.
+template <class Ctx>
+__device__ __forceinline__ void desc_fill(TileDesc<Ctx>& td, uint64_t U, int d, uint64_t tau,
+                                          uint64_t k, uint32_t k_max, int* err) {
+  td.U = U;
+  td.d = d;
+  td.tau = uint32_t(tau);
+  td.W = tile_width(U, d);
+  td.lo = node_bound(U, td.W, d, d, tau);
+  td.L = node_bound(U, td.W, d, d, u128(tau) + 1) - td.lo;
+  td.k = uint32_t(k > 0xffffffffull ? 0xffffffffull : k);
+  td.flags = 2;
+  if (k == 0) return;
+  if (k > 0xffffffffull) {
+    set_error(err, ST_INTERNAL);
+    return;
+  }
+  if (k > td.L) {
+    set_error(err, ST_INTERNAL);
+    return;
+  }
+  if (k > k_max) {
+    td.flags = 1;
+    return;
+  }
+  td.flags = 0;
+  uint32_t nb = 32;
+  while (nb < k) nb <<= 1;
+  td.nb = nb;
+  // bucket multiplier floor(2^64 nb / L) (0 means: bucket = value)
+  td.nbmul = (td.L <= nb) ? 0 : uint64_t(double(nb) * 0x1p64 / double(td.L));
+}
 
 template <class Geom>
 __global__ void __launch_bounds__(256)
-    tile_desc_kernel(Geom g, uint64_t c_begin, int d, uint32_t k_max,
+    tile_desc_kernel(Geom g, uint64_t c_begin, int d, uint32_t k_max, uint64_t seed,
                      const uint64_t* __restrict__ tile_cnt, const uint64_t* __restrict__ tile_off,
-                     uint64_t ntiles, TileDesc<Geom>* __restrict__ desc, unsigned long long* big,
-                     unsigned long long* nbig, int* err) {
+                     uint64_t ntiles, TileDesc<typename Geom::Ctx>* __restrict__ desc,
+                     unsigned long long* big, unsigned long long* nbig, int* err) {
   for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < ntiles;
        t += uint64_t(gridDim.x) * blockDim.x) {
-    TileDesc<Geom> td;
-    td.k = 0;
-    const uint64_t k = tile_cnt[t];
-    if (k > k_max) {
-      big[atomicAdd(nbig, 1ull)] = t;
-    } else if (k > 0) {
-      const uint64_t c = c_begin + (t >> d);
-      const uint64_t tau = t & ((uint64_t(1) << d) - 1);
-      const uint64_t U = g.universe(c);
-      const uint64_t W = tile_width(U, d);
-      td.lo = node_bound(U, W, d, d, tau);
-      td.L = node_bound(U, W, d, d, u128(tau) + 1) - td.lo;
-      if (k > td.L) {
-        set_error(err, ST_INTERNAL);
-      } else {
-        td.k = uint32_t(k);
-        td.base = tile_off[t];
-        td.node = (g.chunk_id(c) << 32) | ((uint64_t(1) << d) + tau);
-        uint32_t nb = 32;
-        while (nb < k) nb <<= 1;
-        td.nb = nb;
-        // bucket multiplier floor(2^64 nb / L) (0 means: bucket = value)
-        td.nbmul = (td.L <= nb) ? 0 : uint64_t(double(nb) * 0x1p64 / double(td.L));
-        td.gx = g.ctx(c);
-      }
-    }
+    TileDesc<typename Geom::Ctx> td;
+    const uint64_t c = c_begin + (t >> d);
+    const uint64_t tau = t & ((uint64_t(1) << d) - 1);
+    desc_fill(td, g.universe(c), d, tau, tile_cnt[t], k_max, err);
+    td.base = tile_off[t];
+    td.cid = g.chunk_id(c);
+    td.seed = seed;
+    td.gx = g.ctx(c);
+    if (td.flags == 1) big[atomicAdd(nbig, 1ull)] = t;
     desc[t] = td;
   }
 }
@@ -120,11 +141,13 @@ struct FastSmem {
   uint32_t bitT[K_MAX / 32], bitJ[K_MAX / 32];
 };
 
-template <class Geom, class Sink, bool DIGEST>
+// TILE_SEED: every tile carries its own seed (batched instances); otherwise
+// the round keys of the one seed come in as a kernel parameter.
+template <class Geom, class Sink, bool DIGEST, bool TILE_SEED>
 __global__ void __launch_bounds__(FAST_THREADS, 5)
-    leaf_fast_kernel(Geom g, Sink sink, int d, uint64_t seed, RoundKeys rk,
-                     const TileDesc<Geom>* __restrict__ desc, uint64_t ntiles, int* err,
-                     DigestOut dig) {
+    leaf_fast_kernel(Geom g, Sink sink, int d, RoundKeys rk,
+                     const TileDesc<typename Geom::Ctx>* __restrict__ desc, uint64_t ntiles,
+                     int* err, DigestOut dig) {
   __shared__ FastSmem sm;
   __shared__ unsigned bh[65];
   __shared__ unsigned long long red_d[FAST_THREADS / 32];
@@ -137,10 +160,11 @@ __global__ void __launch_bounds__(FAST_THREADS, 5)
     reinterpret_cast<unsigned*>(sm.hist)[b] = 0;
   __syncthreads();
   for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const TileDesc<Geom> td = desc[t];
-    if (td.k == 0) continue;  // uniform over the block
+    const TileDesc<typename Geom::Ctx> td = desc[t];
+    if (td.flags != 0) continue;  // uniform over the block
     const uint32_t k = td.k, nb = td.nb;
-    const uint64_t L = td.L, Lk = L - k, node = td.node, nbmul = td.nbmul;
+    const uint64_t L = td.L, Lk = L - k, node = td.node(td.d, td.tau), nbmul = td.nbmul;
+    const uint64_t seed = td.seed;
 
     // ---- 1./2. draws in registers, bucket counts and slots
     uint64_t x[2 * FAST_PAIRS];
@@ -150,7 +174,11 @@ __global__ void __launch_bounds__(FAST_THREADS, 5)
       const uint32_t i = 2 * (tid + FAST_THREADS * s);
       if (i >= k) break;
       uint32_t w[4];
-      philox10_rk(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, rk, w);
+      if (TILE_SEED)
+        philox10(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, uint32_t(seed),
+                 uint32_t(seed >> 32), w);
+      else
+        philox10_rk(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, rk, w);
       x[2 * s] = lemire_draw((uint64_t(w[0]) << 32) | w[1], Lk + i + 1, seed, node, i);
       x[2 * s + 1] = (i + 1 < k)
                          ? lemire_draw((uint64_t(w[2]) << 32) | w[3], Lk + i + 2, seed, node, i + 1)

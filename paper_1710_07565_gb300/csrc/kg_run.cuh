@@ -43,24 +43,25 @@ inline int launch_leaf(const Geom& g, const Sink& sink, uint64_t c_begin, int d,
   unsigned long long* nbig = ws.alloc<unsigned long long>(1);
   if (!ws.ok()) return ST_CUDA;
   if (cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), s) != cudaSuccess) return ST_CUDA;
-  TileDesc<Geom>* desc = ws.alloc<TileDesc<Geom>>(T);
+  using Desc = TileDesc<typename Geom::Ctx>;
+  Desc* desc = ws.alloc<Desc>(T);
   if (!ws.ok()) return ST_CUDA;
   {
     ProfScope ps(PROF_OTHER, s);
     tile_desc_kernel<Geom><<<grid_for(T, 256, 152 * 32), 256, 0, s>>>(
-        g, c_begin, d, k_max, tile_cnt, tile_off, T, desc, big, nbig, err);
+        g, c_begin, d, k_max, seed, tile_cnt, tile_off, T, desc, big, nbig, err);
     if (launch_ok()) return ST_CUDA;
   }
   const unsigned grid = unsigned(T < 0x7fffffffull ? T : 0x7fffffffull);
   {
     ProfScope ps(PROF_LEAF, s);
-    leaf_fast_kernel<Geom, Sink, DIGEST><<<grid, FAST_THREADS, 0, s>>>(
-        g, sink, d, seed, round_keys(seed), desc, T, err, dig);
+    leaf_fast_kernel<Geom, Sink, DIGEST, false><<<grid, FAST_THREADS, 0, s>>>(
+        g, sink, d, round_keys(seed), desc, T, err, dig);
     if (launch_ok()) return ST_CUDA;
   }
   ProfScope ps(PROF_OTHER, s);
-  leaf_resplit_kernel<Geom, Sink, DIGEST><<<152, LEAF_THREADS, 0, s>>>(
-      g, sink, c_begin, d, k_max, seed, tile_cnt, tile_off, err, dig, big, nbig);
+  leaf_resplit_kernel<Geom, Sink, DIGEST, Desc><<<152, LEAF_THREADS, 0, s>>>(
+      g, sink, k_max, desc, err, dig, big, nbig);
   return launch_ok();
 }
 

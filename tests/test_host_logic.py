@@ -142,3 +142,23 @@ def test_row_bounds_without_wide_division(sh):
         cs = set(range(0, min(P, 50) + 1)) | {P} | {int(x) for x in rng.integers(0, P + 1, 200)}
         for c in cs:
             assert sh.sh_row_bound(n, P, c) == c * n // P, (n, P, c)
+
+
+def test_workload_generators_are_deterministic_and_in_range():
+    from paper_1710_07565_gb300 import workloads
+    a = workloads.batched_instances(4096)
+    b = workloads.batched_instances(4096)
+    assert a == b and len(a) == 4096
+    for q in a:
+        assert 256 <= q["n"] <= 1 << 20
+        pairs = q["n"] * (q["n"] - 1) // (2 if q["undirected"] else 1)
+        assert 0 <= q["m"] <= pairs
+        assert 1 <= q["chunks"] <= (32 if q["undirected"] else 64) and q["chunks"] <= q["n"]
+        deg = (2 * q["m"] if q["undirected"] else q["m"]) / q["n"]
+        assert 1.9 <= deg <= 64.1 or q["m"] == pairs
+    frac_und = sum(q["undirected"] for q in a) / len(a)
+    assert 0.45 < frac_und < 0.55
+    r = workloads.serving_requests(2000, 100.0)
+    assert r == workloads.serving_requests(2000, 100.0)
+    assert all(r[i]["arrival"] < r[i + 1]["arrival"] for i in range(len(r) - 1))
+    assert all(1 << 10 <= q["n"] <= 1 << 26 for q in r)
