@@ -197,6 +197,52 @@ kg_status kg_batch_get_tuning(const kg_batch* batch, uint32_t* tree_threads,
                               uint32_t* leaf_grid_cap);
 kg_status kg_batch_destroy(kg_batch* batch);
 
+/* Exact size of a G(n,p) output before generating it: *d_count (device)
+ * receives the number of entries kg_gnp_ex would write with the same
+ * arguments (both directions for undirected), from the same skip walks
+ * without storing them. */
+kg_status kg_gnp_count(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
+                       uint32_t k_leaf, uint64_t* d_count, void* stream);
+
+/*
+ * Serving: a continuous-batching request loop (host scheduling, device work).
+ * kg_server_create reserves `budget_bytes` of device memory for outputs and
+ * `streams` CUDA streams.  kg_server_submit queues a request; a G(n,p)
+ * request is first sized exactly on the device (kg_gnp_count).  Each
+ * kg_server_poll admits waiting requests in arrival order while their exact
+ * output (entries * 2 * id_bytes bytes) fits in the free budget, launches
+ * them on the streams (so new requests overlap with running ones), and
+ * reports finished requests: the output is reduced on the device to its
+ * digest (as kg_edge_digest), copied to host memory, and its budget freed.
+ * Times are milliseconds since kg_server_create (host clock).  The
+ * generators' own scratch comes from the device's stream-ordered pool, not
+ * from the budget.  A request larger than the whole budget finishes with
+ * KG_ERR_CAPACITY.  The digest of a request does not depend on what else is
+ * running.  Not thread-safe: one host thread drives a server.
+ */
+typedef struct kg_request {
+  int32_t model;      /* 0: G(n,m), 1: G(n,p) */
+  int32_t undirected; /* 0 or 1 */
+  uint64_t n, m;      /* m for G(n,m) */
+  double p;           /* p for G(n,p) */
+  uint64_t seed;
+  uint32_t chunks;
+  int32_t id_bytes;   /* 4 or 8 */
+} kg_request;
+typedef struct kg_result {
+  uint64_t id, entries, digest;
+  double t_submit_ms, t_admit_ms, t_done_ms;
+  int32_t status, pad;
+} kg_result;
+typedef struct kg_server kg_server;
+kg_status kg_server_create(uint64_t budget_bytes, uint32_t streams, kg_server** out_server);
+kg_status kg_server_submit(kg_server* server, const kg_request* request, uint64_t* id_out);
+kg_status kg_server_poll(kg_server* server, kg_result* h_results, uint32_t max_results,
+                         uint32_t* n_results);
+kg_status kg_server_pending(const kg_server* server, uint32_t* sizing, uint32_t* waiting,
+                            uint32_t* running, uint64_t* bytes_in_use);
+kg_status kg_server_destroy(kg_server* server);
+
 /* Order-independent digest of an edge list (see kg_gnm_directed_range):
  * *d_digest = sum of splitmix64(u xor rotl64(v, 32)) over `count` pairs. */
 kg_status kg_edge_digest(const void* d_edges, uint64_t count, int id_bytes, uint64_t* d_digest,

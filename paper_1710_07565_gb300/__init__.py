@@ -84,6 +84,18 @@ def lib() -> ctypes.CDLL:
             L.kg_batch_get_tuning.restype = ctypes.c_int
             L.kg_batch_destroy.argtypes = [vp]
             L.kg_batch_destroy.restype = ctypes.c_int
+            L.kg_gnp_count.argtypes = [i32, u64, dbl, u64, u32, u32, vp, vp]
+            L.kg_gnp_count.restype = ctypes.c_int
+            L.kg_server_create.argtypes = [u64, u32, ctypes.POINTER(vp)]
+            L.kg_server_create.restype = ctypes.c_int
+            L.kg_server_submit.argtypes = [vp, vp, ctypes.POINTER(u64)]
+            L.kg_server_submit.restype = ctypes.c_int
+            L.kg_server_poll.argtypes = [vp, vp, u32, ctypes.POINTER(u32)]
+            L.kg_server_poll.restype = ctypes.c_int
+            L.kg_server_pending.argtypes = [vp, vp, vp, vp, vp]
+            L.kg_server_pending.restype = ctypes.c_int
+            L.kg_server_destroy.argtypes = [vp]
+            L.kg_server_destroy.restype = ctypes.c_int
             L.kg_status_str.argtypes = [ctypes.c_int]
             L.kg_status_str.restype = ctypes.c_char_p
             L.kg_launch_count.argtypes = []
@@ -243,6 +255,80 @@ def kg_batch_get_tuning(h):
 
 def kg_batch_destroy(h):
     return _call("kg_batch_destroy", h)
+
+
+def kg_gnp_count(undirected, n, p, seed, chunks, k_leaf, d_count, stream):
+    return _call("kg_gnp_count", int(undirected), n, p, seed, chunks, k_leaf, d_count, stream)
+
+
+class kg_request(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("undirected", ctypes.c_int32), ("n", ctypes.c_uint64),
+                ("m", ctypes.c_uint64), ("p", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("chunks", ctypes.c_uint32), ("id_bytes", ctypes.c_int32)]
+
+
+class kg_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("entries", ctypes.c_uint64), ("digest", ctypes.c_uint64),
+                ("t_submit_ms", ctypes.c_double), ("t_admit_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double), ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+def kg_server_create(budget_bytes, streams):
+    h = ctypes.c_void_p()
+    _call("kg_server_create", budget_bytes, streams, ctypes.byref(h))
+    return h
+
+
+def kg_server_submit(h, req: dict, id_bytes=4) -> int:
+    r = kg_request(1 if req["model"] == "gnp" else 0, 1 if req["undirected"] else 0, req["n"],
+                   req.get("m", 0), req.get("p", 0.0), req["seed"], req["chunks"], id_bytes)
+    out = ctypes.c_uint64()
+    _call("kg_server_submit", h, ctypes.byref(r), ctypes.byref(out))
+    return out.value
+
+
+def kg_server_poll(h, max_results=4096):
+    buf = (kg_result * max_results)()
+    n = ctypes.c_uint32()
+    _call("kg_server_poll", h, ctypes.cast(buf, ctypes.c_void_p), max_results, ctypes.byref(n))
+    return [{"id": buf[i].id, "entries": buf[i].entries, "digest": buf[i].digest,
+             "t_submit_ms": buf[i].t_submit_ms, "t_admit_ms": buf[i].t_admit_ms,
+             "t_done_ms": buf[i].t_done_ms, "status": buf[i].status} for i in range(n.value)]
+
+
+def kg_server_pending(h):
+    a, b, c, d = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+    _call("kg_server_pending", h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d))
+    return {"sizing": a.value, "waiting": b.value, "running": c.value, "bytes_in_use": d.value}
+
+
+def kg_server_destroy(h):
+    return _call("kg_server_destroy", h)
+
+
+def serve(requests, budget_bytes, streams=8, id_bytes=4, realtime=True, clock=None):
+    """Drive a server over `requests` (dicts with an 'arrival' time in seconds):
+    submit each at its arrival (realtime) or all at once, poll until all are
+    done.  Returns the per-request results (by id order of submission)."""
+    import time
+    h = kg_server_create(budget_bytes, streams)
+    results = {}
+    try:
+        t0 = time.perf_counter()
+        i = 0
+        idmap = {}
+        while len(results) < len(requests):
+            now = time.perf_counter() - t0
+            while i < len(requests) and (not realtime or requests[i]["arrival"] <= now):
+                idmap[kg_server_submit(h, requests[i], id_bytes)] = i
+                i += 1
+            for r in kg_server_poll(h):
+                results[idmap[r["id"]]] = r
+            if i < len(requests) and realtime:
+                time.sleep(0)
+    finally:
+        kg_server_destroy(h)
+    return [results[k] for k in range(len(requests))]
 
 
 # ---------------------------------------------------------------- torch helpers

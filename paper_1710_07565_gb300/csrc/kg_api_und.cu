@@ -182,6 +182,30 @@ static int gnp_impl(const Geom& g, uint64_t C, bool undirected, uint64_t n, cons
   return assemble<Id>(pairs, npairs, 0, n, static_cast<Id*>(d_out), cap, ws, s, err);
 }
 
+// Count pass only: per-tile counts (no slots) and their sum.
+template <class Geom>
+static int gnp_count_impl(const Geom& g, uint64_t C, bool undirected, const GnpPlan& pl0,
+                          uint64_t seed, uint64_t* d_count, cudaStream_t s, int* err) {
+  Workspace ws(s);
+  GnpPlan pl = pl0;
+  pl.cap_t = 0;
+  const uint64_t tiles = C * pl.tiles_per_chunk;
+  uint64_t* cnt = ws.alloc<uint64_t>(tiles);
+  uint64_t* off = ws.alloc<uint64_t>(tiles + 1);
+  if (!ws.ok()) return ST_CUDA;
+  {
+    ProfScope ps(PROF_GNP, s);
+    gnp_tiles<Geom, uint32_t><<<grid_for(tiles, 128, 1u << 20), 128, 0, s>>>(g, pl, seed, C,
+                                                                             nullptr, cnt);
+    if (launch_ok()) return ST_CUDA;
+  }
+  int st = scan_exclusive_u64(cnt, off, tiles, ws, s);
+  if (st) return st;
+  ProfScope ps(PROF_OTHER, s);
+  gnp_total<<<1, 1, 0, s>>>(off + tiles, d_count, nullptr, undirected ? 2 : 1, ~uint64_t(0), err);
+  return launch_ok();
+}
+
 template <class Geom, class Id>
 static int gnp_dispatch_slots(const Geom& g, uint64_t C, bool und, uint64_t n, const GnpPlan& pl,
                               uint64_t seed, void* d_out, uint64_t cap, uint64_t* d_count,
@@ -220,47 +244,56 @@ kg_status kg_gnm_undirected(uint64_t n, uint64_t m, uint64_t seed, uint32_t chun
                               stream);
 }
 
-kg_status kg_gnp_ex(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
-                    uint32_t k_leaf, int id_bytes, void* d_out, uint64_t cap_edges,
-                    uint64_t* d_count, void* stream) {
-  if (!(p >= 0.0 && p <= 1.0) || k_leaf < 2 || !d_count) return KG_ERR_ARG;
-  if (n == 0 || chunks == 0 || uint64_t(chunks) > n) return KG_ERR_ARG;
-  if (id_bytes != 4 && id_bytes != 8) return KG_ERR_ARG;
-  if (id_bytes == 4 && n > (uint64_t(1) << 32)) return KG_ERR_RANGE;
+// Validation and tile plan shared by kg_gnp_ex and kg_gnp_count.
+static int gnp_prepare(int undirected, uint64_t n, double p, uint32_t chunks, uint32_t k_leaf,
+                       int id_bytes, GnpPlan& pl, uint64_t& C) {
+  if (!(p >= 0.0 && p <= 1.0) || k_leaf < 2) return ST_ARG;
+  if (n == 0 || chunks == 0 || uint64_t(chunks) > n) return ST_ARG;
+  if (id_bytes != 4 && id_bytes != 8) return ST_ARG;
+  if (id_bytes == 4 && n > (uint64_t(1) << 32)) return ST_RANGE;
   const uint64_t rows_max = uint64_t((u128(n) + chunks - 1) / chunks);
   u128 Unom;
-  uint64_t C;
   if (undirected) {
-    if (chunks > 65536u || n > (uint64_t(1) << 31)) return KG_ERR_RANGE;
+    if (chunks > 65536u || n > (uint64_t(1) << 31)) return ST_RANGE;
     Unom = u128(rows_max) * rows_max;
     C = uint64_t(chunks) * (chunks + 1) / 2;
   } else {
-    if (chunks > (1u << 24)) return KG_ERR_RANGE;
+    if (chunks > (1u << 24)) return ST_RANGE;
     Unom = u128(rows_max) * (n - 1);
     C = chunks;
   }
-  if (Unom >> 64) return KG_ERR_RANGE;
-  cudaStream_t s = as_stream(stream);
-  if (cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s) != cudaSuccess) return KG_ERR_CUDA;
-  if (p == 0.0 || n < 2) return KG_OK;
-  GnpPlan pl;
+  if (Unom >> 64) return ST_RANGE;
   pl.p = p;
   pl.all = (p >= 1.0);
-  pl.inv_lq = pl.all ? 0.0 : 1.0 / kg_log1m(p);
-  pl.T = pl.all ? (uint64_t(1) << 20) : gnp_tile_len(p, k_leaf);
+  pl.inv_lq = (pl.all || p == 0.0) ? 0.0 : 1.0 / kg_log1m(p);
+  pl.T = pl.all ? (uint64_t(1) << 20) : (p == 0.0 ? (uint64_t(1) << 62) : gnp_tile_len(p, k_leaf));
   pl.tiles_per_chunk = uint64_t((Unom + pl.T - 1) / pl.T);
-  if (pl.tiles_per_chunk > (uint64_t(1) << 32)) return KG_ERR_RANGE;
+  if (pl.tiles_per_chunk > (uint64_t(1) << 32)) return ST_RANGE;
   const u128 tiles = u128(C) * pl.tiles_per_chunk;
-  if (tiles > (u128(1) << 34)) return KG_ERR_RANGE;
+  if (tiles > (u128(1) << 34)) return ST_RANGE;
   uint64_t cap_t = pl.all ? 0 : 2 * uint64_t(k_leaf) + 64;
   if (cap_t > pl.T) cap_t = pl.T;
   const uint64_t slot_bytes = (pl.T <= (uint64_t(1) << 32)) ? 4 : 8;
-  if (uint64_t(tiles) * cap_t * slot_bytes > (uint64_t(4) << 30)) cap_t = 0;  // regenerate tiles
+  // slots above this size: tiles are walked a second time instead
+  if (uint64_t(tiles) * cap_t * slot_bytes > (uint64_t(12) << 30)) cap_t = 0;
   pl.cap_t = uint32_t(cap_t);
+  return ST_OK;
+}
+
+kg_status kg_gnp_ex(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
+                    uint32_t k_leaf, int id_bytes, void* d_out, uint64_t cap_edges,
+                    uint64_t* d_count, void* stream) {
+  if (!d_count) return KG_ERR_ARG;
+  GnpPlan pl;
+  uint64_t C = 0;
+  int st = gnp_prepare(undirected, n, p, chunks, k_leaf, id_bytes, pl, C);
+  if (st) return kg_status(st);
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s) != cudaSuccess) return KG_ERR_CUDA;
+  if (p == 0.0 || n < 2) return KG_OK;
   if (!d_out && cap_edges > 0) return KG_ERR_ARG;
   int* err = device_error_word();
   if (!err) return KG_ERR_CUDA;
-  int st;
   if (undirected) {
     UndGeom g{n, chunks, RowBounds::make(n, chunks)};
     st = id_bytes == 4
@@ -275,6 +308,32 @@ kg_status kg_gnp_ex(int undirected, uint64_t n, double p, uint64_t seed, uint32_
     st = id_bytes == 4
              ? gnp_dispatch_slots<DirGeom, uint32_t>(g, C, false, n, pl, seed, d_out, cap_edges, d_count, s, err)
              : gnp_dispatch_slots<DirGeom, uint64_t>(g, C, false, n, pl, seed, d_out, cap_edges, d_count, s, err);
+  }
+  return kg_status(st);
+}
+
+kg_status kg_gnp_count(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
+                       uint32_t k_leaf, uint64_t* d_count, void* stream) {
+  if (!d_count) return KG_ERR_ARG;
+  GnpPlan pl;
+  uint64_t C = 0;
+  int st = gnp_prepare(undirected, n, p, chunks, k_leaf, 8, pl, C);
+  if (st) return kg_status(st);
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s) != cudaSuccess) return KG_ERR_CUDA;
+  if (p == 0.0 || n < 2) return KG_OK;
+  int* err = device_error_word();
+  if (!err) return KG_ERR_CUDA;
+  if (undirected) {
+    UndGeom g{n, chunks, RowBounds::make(n, chunks)};
+    st = gnp_count_impl(g, C, true, pl, seed, d_count, s, err);
+  } else {
+    DirGeom g;
+    g.n = n;
+    g.P = chunks;
+    g.div = make_div(n - 1);
+    g.rb = RowBounds::make(n, chunks);
+    st = gnp_count_impl(g, C, false, pl, seed, d_count, s, err);
   }
   return kg_status(st);
 }

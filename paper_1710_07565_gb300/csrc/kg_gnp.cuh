@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(128)
       cnt[t] = hi - lo;
       continue;
     }
-    SlotT* sl = slots + t * pl.cap_t;
+    SlotT* sl = slots ? slots + t * pl.cap_t : nullptr;
     const uint32_t cap_t = pl.cap_t;
     cnt[t] = gnp_tile_walk(seed, (g.chunk_id(c) << 32) | tau, lo, hi, pl.inv_lq,
                            [&](uint64_t i, uint64_t x) {

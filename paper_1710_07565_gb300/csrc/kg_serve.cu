@@ -1,0 +1,303 @@
+// Serving: a continuous-batching request loop over the generators.
+//
+// Requests (G(n,m) or G(n,p), directed or undirected) are admitted in arrival
+// order when their exact output size fits in a fixed device budget; the size
+// of a G(n,m) request is m or 2m entries, that of a G(n,p) request is counted
+// first on the device (kg_gnp_count, same skip walks without storing them).
+// Admitted requests run on a set of streams, so requests that arrive while
+// others are on the GPU overlap with them; a request's output is reduced on
+// the device to its order-independent digest, copied to host memory, and its
+// budget released -- which admits the next waiting requests.  Everything is
+// host-side scheduling around the library's own entry points; the state of
+// every request stays on the device until its digest is read.
+#include <algorithm>
+#include <chrono>
+#include <deque>
+#include <map>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/kg.h"
+#include "kg_internal.h"
+
+namespace {
+
+constexpr uint32_t MAX_INFLIGHT = 4096;
+
+enum ReqState { SIZING, WAITING, RUNNING };
+
+struct Req {
+  kg_request q;
+  uint64_t id = 0, entries = 0, bytes = 0, off = 0;
+  ReqState state = WAITING;
+  int stream = 0;
+  uint32_t slot = 0;
+  cudaEvent_t ev = nullptr;
+  double t_submit = 0, t_admit = 0;
+};
+
+}  // namespace
+
+struct kg_server {
+  int device = 0;
+  unsigned char* pool = nullptr;
+  uint64_t budget = 0, in_use = 0;
+  std::map<uint64_t, uint64_t> free_;  // offset -> size, coalesced
+  std::vector<cudaStream_t> streams;
+  uint32_t next_stream = 0;
+  uint64_t next_id = 0;
+  std::deque<uint64_t> waiting;        // admission order
+  std::unordered_map<uint64_t, Req> reqs;
+  uint64_t* d_slots = nullptr;         // per in-flight request: count, digest
+  uint64_t* h_slots = nullptr;         // pinned mirrors
+  std::vector<uint32_t> free_slots;
+  std::vector<cudaEvent_t> free_events;
+  std::chrono::steady_clock::time_point t0;
+
+  double now_ms() const {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  bool alloc(uint64_t bytes, uint64_t& off) {
+    bytes = (bytes + 255) & ~uint64_t(255);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        off = it->first;
+        const uint64_t rest = it->second - bytes;
+        free_.erase(it);
+        if (rest) free_[off + bytes] = rest;
+        in_use += bytes;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t bytes) {
+    bytes = (bytes + 255) & ~uint64_t(255);
+    in_use -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  cudaEvent_t event() {
+    if (!free_events.empty()) {
+      cudaEvent_t e = free_events.back();
+      free_events.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    return e;
+  }
+  cudaStream_t pick_stream(int& idx) {
+    idx = int(next_stream++ % streams.size());
+    return streams[idx];
+  }
+};
+
+static uint64_t req_bytes(const kg_request& q, uint64_t entries) {
+  return entries * 2 * uint64_t(q.id_bytes);
+}
+
+// Launch the generator, then the digest of its output, then the digest's copy.
+static kg_status launch(kg_server* S, Req& r) {
+  const kg_request& q = r.q;
+  cudaStream_t s = S->pick_stream(r.stream);
+  void* out = S->pool + r.off;
+  kg_status st;
+  if (q.model == 0) {
+    st = q.undirected ? kg_gnm_undirected(q.n, q.m, q.seed, q.chunks, q.id_bytes, out, r.entries, s)
+                      : kg_gnm_directed(q.n, q.m, q.seed, q.chunks, q.id_bytes, out, r.entries, s);
+  } else {
+    st = kg_gnp_ex(q.undirected, q.n, q.p, q.seed, q.chunks, 1024, q.id_bytes, out, r.entries,
+                   S->d_slots + 2 * r.slot, s);
+  }
+  if (st != KG_OK) return st;
+  st = kg_edge_digest(out, r.entries, q.id_bytes, S->d_slots + 2 * r.slot + 1, s);
+  if (st != KG_OK) return st;
+  if (cudaMemcpyAsync(S->h_slots + 2 * r.slot + 1, S->d_slots + 2 * r.slot + 1, 8,
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return KG_ERR_CUDA;
+  r.ev = S->event();
+  if (cudaEventRecord(r.ev, s) != cudaSuccess) return KG_ERR_CUDA;
+  return KG_OK;
+}
+
+static void finish(kg_server* S, Req& r, kg_status st, kg_result* out) {
+  out->id = r.id;
+  out->entries = r.entries;
+  out->digest = (st == KG_OK) ? S->h_slots[2 * r.slot + 1] : 0;
+  out->t_submit_ms = r.t_submit;
+  out->t_admit_ms = r.t_admit;
+  out->t_done_ms = S->now_ms();
+  out->status = st;
+  out->pad = 0;
+  if (r.state == RUNNING) S->release(r.off, r.bytes);
+  if (r.ev) S->free_events.push_back(r.ev);
+  S->free_slots.push_back(r.slot);
+}
+
+extern "C" {
+
+kg_status kg_server_create(uint64_t budget_bytes, uint32_t nstreams, kg_server** out) {
+  if (!out || budget_bytes == 0 || nstreams == 0 || nstreams > 64) return KG_ERR_ARG;
+  *out = nullptr;
+  kg_server* S = new kg_server();
+  S->t0 = std::chrono::steady_clock::now();
+  if (cudaGetDevice(&S->device) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&S->pool), budget_bytes) != cudaSuccess) {
+    delete S;
+    return KG_ERR_CUDA;
+  }
+  S->budget = budget_bytes;
+  S->free_[0] = budget_bytes & ~uint64_t(255);
+  if (cudaMalloc(reinterpret_cast<void**>(&S->d_slots), 16 * MAX_INFLIGHT) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&S->h_slots), 16 * MAX_INFLIGHT) != cudaSuccess) {
+    kg_server_destroy(S);
+    return KG_ERR_CUDA;
+  }
+  for (uint32_t i = 0; i < MAX_INFLIGHT; ++i) S->free_slots.push_back(MAX_INFLIGHT - 1 - i);
+  for (uint32_t i = 0; i < nstreams; ++i) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      kg_server_destroy(S);
+      return KG_ERR_CUDA;
+    }
+    S->streams.push_back(s);
+  }
+  *out = S;
+  return KG_OK;
+}
+
+kg_status kg_server_destroy(kg_server* S) {
+  if (!S) return KG_OK;
+  for (cudaStream_t s : S->streams) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  for (auto& kv : S->reqs)
+    if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+  for (cudaEvent_t e : S->free_events) cudaEventDestroy(e);
+  if (S->pool) cudaFree(S->pool);
+  if (S->d_slots) cudaFree(S->d_slots);
+  if (S->h_slots) cudaFreeHost(S->h_slots);
+  delete S;
+  return KG_OK;
+}
+
+kg_status kg_server_submit(kg_server* S, const kg_request* q, uint64_t* id_out) {
+  if (!S || !q || (q->model != 0 && q->model != 1) || (q->id_bytes != 4 && q->id_bytes != 8))
+    return KG_ERR_ARG;
+  if (S->free_slots.empty()) return KG_ERR_CAPACITY;
+  Req r;
+  r.q = *q;
+  r.id = S->next_id++;
+  r.t_submit = S->now_ms();
+  r.slot = S->free_slots.back();
+  S->free_slots.pop_back();
+  if (q->model == 0) {
+    r.entries = q->undirected ? 2 * q->m : q->m;
+    r.state = WAITING;
+    S->waiting.push_back(r.id);
+  } else {
+    // exact size first: the count pass, its result copied to pinned memory
+    cudaStream_t s = S->pick_stream(r.stream);
+    kg_status st = kg_gnp_count(q->undirected, q->n, q->p, q->seed, q->chunks, 1024,
+                                S->d_slots + 2 * r.slot, s);
+    if (st == KG_OK &&
+        cudaMemcpyAsync(S->h_slots + 2 * r.slot, S->d_slots + 2 * r.slot, 8, cudaMemcpyDeviceToHost,
+                        s) != cudaSuccess)
+      st = KG_ERR_CUDA;
+    if (st != KG_OK) {
+      S->free_slots.push_back(r.slot);
+      return st;
+    }
+    r.ev = S->event();
+    cudaEventRecord(r.ev, s);
+    r.state = SIZING;
+  }
+  if (id_out) *id_out = r.id;
+  S->reqs.emplace(r.id, r);
+  return KG_OK;
+}
+
+// One scheduling pass: sized G(n,p) requests join the queue, waiting requests
+// are admitted in order while their bytes fit, finished requests are reported.
+kg_status kg_server_poll(kg_server* S, kg_result* out, uint32_t max_out, uint32_t* n_out) {
+  if (!S || !n_out || (max_out && !out)) return KG_ERR_ARG;
+  *n_out = 0;
+  std::vector<uint64_t> sized;
+  for (auto& kv : S->reqs) {
+    Req& r = kv.second;
+    if (r.state == SIZING && cudaEventQuery(r.ev) == cudaSuccess) {
+      r.entries = S->h_slots[2 * r.slot];
+      S->free_events.push_back(r.ev);
+      r.ev = nullptr;
+      r.state = WAITING;
+      sized.push_back(r.id);
+    }
+  }
+  std::sort(sized.begin(), sized.end());
+  for (uint64_t id : sized) S->waiting.push_back(id);
+  // admission (arrival order; a request larger than the whole budget is refused)
+  while (!S->waiting.empty() && *n_out < max_out) {
+    Req& r = S->reqs[S->waiting.front()];
+    r.bytes = req_bytes(r.q, r.entries);
+    if (r.bytes > S->budget) {
+      S->waiting.pop_front();
+      finish(S, r, KG_ERR_CAPACITY, out + (*n_out)++);
+      S->reqs.erase(r.id);
+      continue;
+    }
+    if (!S->alloc(r.bytes ? r.bytes : 256, r.off)) break;
+    if (!r.bytes) r.bytes = 256;
+    S->waiting.pop_front();
+    r.t_admit = S->now_ms();
+    r.state = RUNNING;
+    const kg_status st = launch(S, r);
+    if (st != KG_OK) {
+      finish(S, r, st, out + (*n_out)++);
+      S->reqs.erase(r.id);
+    }
+  }
+  // completions
+  std::vector<uint64_t> done;
+  for (auto& kv : S->reqs)
+    if (kv.second.state == RUNNING && cudaEventQuery(kv.second.ev) == cudaSuccess)
+      done.push_back(kv.first);
+  std::sort(done.begin(), done.end());
+  for (uint64_t id : done) {
+    if (*n_out >= max_out) break;
+    Req& r = S->reqs[id];
+    finish(S, r, KG_OK, out + (*n_out)++);
+    S->reqs.erase(id);
+  }
+  return KG_OK;
+}
+
+kg_status kg_server_pending(const kg_server* S, uint32_t* sizing, uint32_t* waiting,
+                            uint32_t* running, uint64_t* bytes_in_use) {
+  if (!S) return KG_ERR_ARG;
+  uint32_t a = 0, b = 0, c = 0;
+  for (const auto& kv : S->reqs) {
+    if (kv.second.state == SIZING) ++a;
+    if (kv.second.state == WAITING) ++b;
+    if (kv.second.state == RUNNING) ++c;
+  }
+  if (sizing) *sizing = a;
+  if (waiting) *waiting = b;
+  if (running) *running = c;
+  if (bytes_in_use) *bytes_in_use = S->in_use;
+  return KG_OK;
+}
+
+}  // extern "C"
