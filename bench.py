@@ -4,10 +4,12 @@
 Workload (one step): n = 2^36 vertices, m = 2^33 edges, P = 2^16 chunks,
 seed 1, uint64 ids (16 B per edge).  The chunk split tree gives every chunk
 its count; the edges are then generated in 16 slabs of 4096 chunks (about
-2^29 edges = 8 GiB each) into one device slab buffer, and every slab is
-reduced on the device, inside the same kernel, to a per-chunk order-
-independent 64-bit digest and out-degree histogram.  128 GiB of edges are
-written per step, far more than L2, so no flush is needed between steps.
+2^29 edges = 8 GiB each), alternating between two device slab buffers on two
+streams so that one slab's tile tree overlaps the previous slab's leaf
+kernel, and every slab is reduced on the device, inside the same kernel, to
+a per-chunk order-independent 64-bit digest and out-degree histogram.
+128 GiB of edges are written per step, far more than L2, so no flush is
+needed between steps.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -132,6 +134,112 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def _timed(fn, reps, warm=2):
+    """Median milliseconds of fn() over reps runs (CUDA events, current stream)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def other_workloads(kg, serve_requests=1000):
+    """The other configurations, each measured briefly on the same GPU."""
+    import torch
+    from paper_1710_07565_gb300 import workloads
+    s = torch.cuda.current_stream().cuda_stream
+    res = {}
+    # directed G(n,m), n = 2^16, m = 2^20, 64 chunks, uint32 ids (latency-bound)
+    n, m, P = 1 << 16, 1 << 20, 64
+    out = torch.empty((m, 2), dtype=torch.int32, device="cuda")
+    ms = _timed(lambda: kg.kg_gnm_directed(n, m, 1, P, 4, out.data_ptr(), m, s), 20)
+    res["gnm_directed_n2e16_m2e20_P64"] = {"ms": ms, "edges_per_s": m / ms * 1e3}
+    del out
+    # undirected G(n,p), n = 2^20, p = 16/(n-1), 32 x 32 chunks, both directions
+    n = 1 << 20
+    p = 16 / (n - 1)
+    cap = 2 * (8 * n + 20000)
+    out = torch.empty((cap, 2), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    ms = _timed(lambda: kg.kg_gnp_undirected(n, p, 1, 32, 4, out.data_ptr(), cap, cnt.data_ptr(), s), 5)
+    k = int(cnt.item())
+    # FP64 work: one geometric skip (ln + multiply + floor, ~45 double ops) per kept pair
+    res["gnp_undirected_n2e20_avgdeg16_P32"] = {
+        "ms": ms, "entries": k, "entries_per_s": k / ms * 1e3, "write_GBps": k * 8 / ms / 1e6,
+        "bound": "fp64 (one log per kept pair)", "fp64_ops_per_s_est": (k // 2) * 45 / ms * 1e3}
+    del out, cnt
+    kg.check_device_error()
+    # batched: 4096 instances, one launch sequence (CUDA graph) vs 4096 separate calls
+    insts = workloads.batched_instances(4096)
+    h = kg.kg_batch_create(insts)
+    try:
+        total = kg.kg_batch_entries(h)
+        out = torch.empty((total, 2), dtype=torch.int32, device="cuda")
+        dig = torch.zeros(2, dtype=torch.int64, device="cuda")
+        kg.kg_batch_tune(h, out.data_ptr(), total, 1, s)
+        tuning = kg.kg_batch_get_tuning(h)
+        g = torch.cuda.CUDAGraph()
+        st = torch.cuda.Stream()
+        kg.kg_batch_run(h, out.data_ptr(), total, st.cuda_stream)
+        st.synchronize()
+        with torch.cuda.graph(g, stream=st):
+            kg.kg_batch_run(h, out.data_ptr(), total, st.cuda_stream)
+        ms_b = _timed(g.replay, 3, warm=1)
+        kg.kg_edge_digest(out.data_ptr(), total, 4, dig.data_ptr(), s)
+
+        def sequential():
+            pos = 0
+            for q in insts:
+                k = 2 * q["m"] if q["undirected"] else q["m"]
+                f = kg.kg_gnm_undirected if q["undirected"] else kg.kg_gnm_directed
+                f(q["n"], q["m"], q["seed"], q["chunks"], 4, out.data_ptr() + 8 * pos, k, s)
+                pos += k
+        ms_s = _timed(sequential, 2, warm=1)
+        kg.kg_edge_digest(out.data_ptr(), total, 4, dig.data_ptr() + 8, s)
+        same = int(dig[0].item()) == int(dig[1].item())
+        kg.check_device_error()
+        res["batched_4096_instances"] = {
+            "instances": len(insts), "entries": total, "batched_ms": ms_b, "per_instance_ms": ms_s,
+            "speedup": ms_s / ms_b, "graphs_per_s": len(insts) / ms_b * 1e3,
+            "entries_per_s": total / ms_b * 1e3, "identical_output": same,
+            "tuned": {"tree_threads": tuning[0], "leaf_grid_cap": tuning[1]}}
+        del out, dig
+    finally:
+        kg.kg_batch_destroy(h)
+    torch.cuda.empty_cache()
+    # serving: closed-loop capacity, then Poisson arrivals at 0.8 x capacity
+    budget = 64 << 30
+    base = workloads.serving_requests(serve_requests, 1.0)
+    t0 = time.perf_counter()
+    closed = kg.serve([dict(r, arrival=0.0) for r in base], budget, streams=8, realtime=False)
+    dt = time.perf_counter() - t0
+    cap_rps = len(base) / dt
+    reqs = workloads.serving_requests(serve_requests, 0.8 * cap_rps)
+    t0 = time.perf_counter()
+    done = kg.serve(reqs, budget, streams=8, realtime=True)
+    dt2 = time.perf_counter() - t0
+    kg.check_device_error()
+    lat = sorted(r["t_done_ms"] - r["t_submit_ms"] for r in done)
+    ent = sum(r["entries"] for r in done)
+    res["serving"] = {
+        "requests": len(reqs), "budget_GB": budget / 1e9, "streams": 8,
+        "closed_loop_requests_per_s": cap_rps, "closed_loop_entries_per_s": sum(r["entries"] for r in closed) / dt,
+        "poisson_rate_per_s": 0.8 * cap_rps, "requests_per_s": len(reqs) / dt2,
+        "entries_per_s": ent / dt2, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(0.99 * (len(lat) - 1))],
+        "ok": all(r["status"] == 0 for r in done),
+        "sample": f"first {len(reqs)} requests of the seeded 100k-request stream"}
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -140,6 +248,8 @@ def main():
     ap.add_argument("--impl", default="kg", choices=["kg", "reference"])
     ap.add_argument("--ref-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other", action="store_true", help="skip the other configurations")
+    ap.add_argument("--serve-requests", type=int, default=1000)
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -163,19 +273,31 @@ def main():
 
     seed = SEED + rank  # independent replicas (weak scaling, no data-path collective)
     dev = torch.device("cuda", local)
-    s = torch.cuda.current_stream().cuda_stream
-    buf = torch.empty((SLAB_CAP, 2), dtype=torch.int64, device=dev)
+    main = torch.cuda.current_stream()
+    s = main.cuda_stream
+    streams = [torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)]
+    bufs = [torch.empty((SLAB_CAP, 2), dtype=torch.int64, device=dev) for _ in streams]
     counts = torch.zeros(P_CHUNKS, dtype=torch.int64, device=dev)
     digest = torch.zeros(P_CHUNKS, dtype=torch.int64, device=dev)
     hist = torch.zeros((P_CHUNKS, 65), dtype=torch.int64, device=dev)
 
     def step():
         kg.kg_gnm_directed_chunk_counts(N_VERT, M_EDGES, seed, P_CHUNKS, counts.data_ptr(), s)
+        ready = torch.cuda.Event()
+        ready.record(main)
+        for st in streams:
+            st.wait_event(ready)
         for i in range(SLABS):
             c0 = i * CHUNKS_PER_SLAB
+            st = streams[i % 2]
             kg.kg_gnm_directed_range(N_VERT, M_EDGES, seed, P_CHUNKS, c0, c0 + CHUNKS_PER_SLAB,
-                                     counts.data_ptr(), ID_BYTES, buf.data_ptr(), SLAB_CAP,
-                                     digest.data_ptr() + 8 * c0, hist.data_ptr() + 8 * 65 * c0, s)
+                                     counts.data_ptr(), ID_BYTES, bufs[i % 2].data_ptr(), SLAB_CAP,
+                                     digest.data_ptr() + 8 * c0, hist.data_ptr() + 8 * 65 * c0,
+                                     st.cuda_stream)
+        for st in streams:
+            done = torch.cuda.Event()
+            done.record(st)
+            main.wait_event(done)
 
     # warm-up
     for _ in range(args.warmup):
@@ -247,7 +369,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": N_VERT, "m": M_EDGES, "chunks": P_CHUNKS,
-                   "slabs": SLABS, "id_bytes": ID_BYTES,
+                   "slabs": SLABS, "id_bytes": ID_BYTES, "streams": len(streams),
                    "l2": "no flush: 128 GiB of output per step, far above the 129 MB L2"},
         "write_GBps": M_EDGES * 16 * args.steps / (ms / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -261,6 +383,10 @@ def main():
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if world == 1 and not args.no_other:
+        del bufs, counts, digest, hist, h_dig, h_hist
+        torch.cuda.empty_cache()
+        line["other_workloads"] = other_workloads(kg, args.serve_requests)
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seconds=args.ref_seconds)
         line["cpu_baseline"]["vs_value"] = value / line["cpu_baseline"]["value"]
