@@ -3,7 +3,7 @@
 #include <mutex>
 #include <unordered_map>
 
-#include "../../include/kg.h"
+#include "kg.h"
 #include "kg_digest.cuh"
 #include "kg_run.cuh"
 

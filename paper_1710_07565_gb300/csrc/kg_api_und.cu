@@ -1,6 +1,6 @@
 // C ABI: undirected G(n,m) (Sec. 4.2) and G(n,p) (Sec. 4.3), directed and
 // undirected, with the assembly of undirected output in both directions.
-#include "../../include/kg.h"
+#include "kg.h"
 #include "kg_gnp.cuh"
 #include "kg_run.cuh"
 #include "kg_und.cuh"

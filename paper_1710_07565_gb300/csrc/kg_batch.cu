@@ -8,7 +8,7 @@
 #include <algorithm>
 #include <vector>
 
-#include "../../include/kg.h"
+#include "kg.h"
 #include "kg_run.cuh"
 #include "kg_und.cuh"
 

@@ -4,7 +4,7 @@
 #include <mutex>
 #include <vector>
 
-#include "../../include/kg.h"
+#include "kg.h"
 #include "kg_prof.h"
 
 namespace kg {

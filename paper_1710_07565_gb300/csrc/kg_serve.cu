@@ -17,7 +17,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/kg.h"
+#include "kg.h"
 #include "kg_internal.h"
 
 namespace {
