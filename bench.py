@@ -240,6 +240,25 @@ def other_workloads(kg, serve_requests=1000):
     return res
 
 
+def profile_case(kg, C):
+    """Chunks [0, C) of the workload, generated three times with digests
+    (the small case for ncu captures of the leaf kernel: 2^17 C edges)."""
+    import torch
+    s = torch.cuda.current_stream().cuda_stream
+    counts = torch.zeros(P_CHUNKS, dtype=torch.int64, device="cuda")
+    kg.kg_gnm_directed_chunk_counts(N_VERT, M_EDGES, SEED, P_CHUNKS, counts.data_ptr(), s)
+    k = int(counts[:C].sum())
+    out = torch.empty((k, 2), dtype=torch.int64, device="cuda")
+    dig = torch.zeros(C, dtype=torch.int64, device="cuda")
+    hist = torch.zeros((C, 65), dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        kg.kg_gnm_directed_range(N_VERT, M_EDGES, SEED, P_CHUNKS, 0, C, counts.data_ptr(), ID_BYTES,
+                                 out.data_ptr(), k, dig.data_ptr(), hist.data_ptr(), s)
+    torch.cuda.synchronize()
+    kg.check_device_error()
+    print(json.dumps({"profile_chunks": C, "edges": k}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -250,6 +269,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-other", action="store_true", help="skip the other configurations")
     ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--profile-chunks", type=int, default=0,
+                    help="run only chunks [0, C) of the workload three times (a small case "
+                         "for ncu captures of the leaf kernel) and exit")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -264,6 +286,8 @@ def main():
     import paper_1710_07565_gb300 as kg
 
     torch.cuda.set_device(local)
+    if args.profile_chunks:
+        return profile_case(kg, args.profile_chunks)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 

@@ -81,6 +81,20 @@ struct BatchSink {
     w.y = uint32_t(v);
     reinterpret_cast<uint2*>(dst)[pos] = w;
   }
+  // whether slots [base, base + k) exist (base may carry SCRATCH_BIT)
+  __device__ __forceinline__ bool fits(uint64_t base, uint64_t k) const {
+    const uint64_t cap = (base & SCRATCH_BIT) ? cap_scratch : cap_out;
+    base &= ~SCRATCH_BIT;
+    return base <= cap && k <= cap - base;
+  }
+  // store to a slot already checked by fits()
+  __device__ __forceinline__ void put(uint64_t pos, uint64_t u, uint64_t v) const {
+    uint32_t* dst = (pos & SCRATCH_BIT) ? scratch : out;
+    uint2 w;
+    w.x = uint32_t(u);
+    w.y = uint32_t(v);
+    reinterpret_cast<uint2*>(dst)[pos & ~SCRATCH_BIT] = w;
+  }
   __device__ __forceinline__ uint64_t read_u(uint64_t pos) const {
     const uint32_t* src = (pos & SCRATCH_BIT) ? scratch : out;
     return src[2 * (pos & ~SCRATCH_BIT)];

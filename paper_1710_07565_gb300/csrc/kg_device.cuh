@@ -505,25 +505,37 @@ __device__ __forceinline__ uint64_t popcount_bits_warp(uint64_t seed, uint64_t n
 // Lemire: high word of x * range; reject when the low word is below
 // (2^64 - range) mod range; retry r draws u64 #i of the stream tagged
 // TAG_LEAF | r << 8.  `x` is the leaf stream's u64 #i.
+__host__ __device__ __forceinline__ uint64_t mul_hi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+  return __umul64hi(a, b);
+#else
+  return uint64_t((u128(a) * b) >> 64);
+#endif
+}
+
+// 2^64 mod r (= (2^64 - r) mod r, Lemire's threshold) by doubling 1 modulo r
+// 64 times; only the rejection branch needs it, and it keeps that branch free
+// of a division routine.
+__host__ __device__ __forceinline__ uint64_t pow2_64_mod(uint64_t r) {
+  uint64_t rem = r == 1 ? 0 : 1;
+  for (int b = 0; b < 64; ++b) {
+    const uint64_t t = rem << 1;
+    rem = ((rem >> 63) || t >= r) ? t - r : t;
+  }
+  return rem;
+}
+
 __host__ __device__ __forceinline__ uint64_t lemire_draw(uint64_t x, uint64_t range, uint64_t seed,
                                                          uint64_t node, uint64_t i) {
-#ifdef __CUDA_ARCH__
-  uint64_t hi = __umul64hi(x, range);
-#else
-  uint64_t hi = uint64_t((u128(x) * range) >> 64);
-#endif
+  uint64_t hi = mul_hi64(x, range);
   uint64_t lo = x * range;
-  if (lo < range) {
-    const uint64_t thr = (0 - range) % range;
+  if (lo < range) {  // probability below range / 2^64
+    const uint64_t thr = pow2_64_mod(range);
     uint32_t r = 1;
     while (lo < thr) {
       x = stream_u64(seed, node, TAG_LEAF | (r << 8), i);
       ++r;
-#ifdef __CUDA_ARCH__
-      hi = __umul64hi(x, range);
-#else
-      hi = uint64_t((u128(x) * range) >> 64);
-#endif
+      hi = mul_hi64(x, range);
       lo = x * range;
     }
   }

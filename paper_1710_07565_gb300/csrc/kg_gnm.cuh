@@ -177,6 +177,24 @@ struct PairSink {
       __stcs(reinterpret_cast<ulonglong2*>(out) + pos, w);
     }
   }
+  // whether slots [base, base + k) exist
+  __device__ __forceinline__ bool fits(uint64_t base, uint64_t k) const {
+    return base <= cap && k <= cap - base;
+  }
+  // store to a slot already checked by fits()
+  __device__ __forceinline__ void put(uint64_t pos, uint64_t u, uint64_t v) const {
+    if (sizeof(Id) == 4) {
+      uint2 w;
+      w.x = uint32_t(u);
+      w.y = uint32_t(v);
+      reinterpret_cast<uint2*>(out)[pos] = w;
+    } else {
+      ulonglong2 w;
+      w.x = u;
+      w.y = v;
+      __stcs(reinterpret_cast<ulonglong2*>(out) + pos, w);
+    }
+  }
   __device__ __forceinline__ uint64_t read_u(uint64_t pos) const {
     if (pos >= cap) return ~uint64_t(0);
     return sizeof(Id) == 4 ? uint64_t(reinterpret_cast<const uint2*>(out)[pos].x)

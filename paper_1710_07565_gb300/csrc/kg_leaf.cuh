@@ -1,18 +1,22 @@
-// Hot leaf kernel: Floyd's sampler on one tile per block of 128 threads.
+// Hot leaf kernel: Floyd's sampler on one tile per block of 256 threads.
 //
 // Per tile of k <= k_max samples in a universe [lo, lo + L):
 //   1. draw i (uniform on [0, L-k+i], Lemire) -- thread t owns the draw pairs
-//      2(t + 128 s), 2(t + 128 s) + 1 that share one Philox block; the values
+//      2(t + 256 s), 2(t + 256 s) + 1 that share one Philox block; the values
 //      stay in registers;
-//   2. bucket b(x) = floor(x nb / L) (a multiplier, monotone in x), counted
-//      with shared-memory atomics that also hand each draw its slot;
-//   3. exclusive scan of the bucket counts; scatter into A;
-//   4. each draw's final rank = bucket start + #{smaller values in its bucket}
-//      + #{equal values at a lower slot}; written to B -- B is the sorted
-//      multiset, and any equal pair means Floyd replaced a value;
-//   5. if all draws are distinct the sample is exactly {t_i}; otherwise the
+//   2. bucket b(x), monotone in x, over nb >= 2k equal-width buckets, counted
+//      with shared-memory atomics on packed 16-bit counters that also hand
+//      each draw its slot in the bucket;
+//   3. exclusive scan of the counts (16-byte groups per thread);
+//   4. scatter to A[start(b) + slot]: A is sorted up to the order inside
+//      buckets;
+//   5. the draw at slot 0 of every bucket with several values sorts that
+//      bucket in place (mean occupancy <= 1/2, so buckets are tiny); an equal
+//      pair means Floyd replaced a value;
+//   6. if all draws are distinct the sample is exactly {t_i}; otherwise the
 //      replacements are resolved in draw order (rare when k^2 << L);
-//   6. B[r] -> (u, v) -> 16- or 8-byte stores to consecutive output slots.
+//   7. A[r] -> (u, v) -> 16- or 8-byte stores to consecutive output slots,
+//      with the order-independent digest and the row runs when asked.
 #pragma once
 #include "kg_gnm.cuh"
 
@@ -57,13 +61,20 @@ __device__ __forceinline__ void philox10_rk(uint32_t c0, uint32_t c1, uint32_t c
   w[3] = c3;
 }
 
-// Bucket of a draw: floor(v * nbmul / 2^64) clamped to nb-1, or v itself
-// when the universe has at most nb values.  Monotone in v.
-__device__ __forceinline__ uint32_t bucket_of(uint64_t v, uint64_t nbmul, uint32_t nb) {
-  if (!nbmul) return uint32_t(v);
-  const uint64_t q = __umul64hi(v, nbmul);
-  return q < nb ? uint32_t(q) : nb - 1;
+// Bucket of a draw, monotone in v: the high word of (v >> bsh) * bmul, or v
+// itself when the universe has at most nb values (bmul = 0).  With
+// L' = ((L-1) >> bsh) + 1 <= 2^32 and bmul = floor(2^32 nb / L'), every
+// v < L lands in [0, nb) and the buckets have equal widths (up to rounding).
+__device__ __forceinline__ uint32_t bucket_of(uint64_t v, uint32_t bsh, uint32_t bmul) {
+  return bmul ? __umulhi(uint32_t(v >> bsh), bmul) : uint32_t(v);
 }
+
+// Buckets per tile: at least twice k (mean occupancy <= 1/2) and at least
+// FAST_THREADS * 8, so that every thread owns whole 16-byte groups of packed
+// 16-bit counters in the scan.
+constexpr uint32_t NB_MIN = 2048;
+constexpr uint32_t NB_MAX = 2 * K_MAX < NB_MIN ? NB_MIN : 2 * K_MAX;
+static_assert(NB_MIN % (8 * FAST_THREADS) == 0, "whole 16-byte counter groups per thread");
 
 // Per-tile parameters, computed for all tiles at once (tile_desc_kernel, or
 // the batched engine's descriptor kernel) so that the leaf blocks start
@@ -71,8 +82,8 @@ __device__ __forceinline__ uint32_t bucket_of(uint64_t v, uint64_t nbmul, uint32
 // (left to the re-split kernel), 2 = nothing to do.
 template <class Ctx>
 struct TileDesc {
-  uint64_t lo, L, base, cid, nbmul, U, W, seed;
-  uint32_t k, nb, tau;
+  uint64_t lo, L, base, cid, U, W, seed;
+  uint32_t k, nb, tau, bmul, bsh;
   int d, flags;
   Ctx gx;
   __host__ __device__ __forceinline__ uint64_t node(int level, uint64_t j) const {
@@ -92,6 +103,9 @@ __device__ __forceinline__ void desc_fill(TileDesc<Ctx>& td, uint64_t U, int d, 
   td.L = node_bound(U, td.W, d, d, u128(tau) + 1) - td.lo;
   td.k = uint32_t(k > 0xffffffffull ? 0xffffffffull : k);
   td.flags = 2;
+  td.nb = NB_MIN;
+  td.bmul = 0;
+  td.bsh = 0;
   if (k == 0) return;
   if (k > 0xffffffffull) {
     set_error(err, ST_INTERNAL);
@@ -106,11 +120,15 @@ __device__ __forceinline__ void desc_fill(TileDesc<Ctx>& td, uint64_t U, int d, 
     return;
   }
   td.flags = 0;
-  uint32_t nb = 32;
-  while (nb < k) nb <<= 1;
+  uint32_t nb = NB_MIN;
+  while (nb < 2 * k) nb <<= 1;
   td.nb = nb;
-  // bucket multiplier floor(2^64 nb / L) (0 means: bucket = value)
-  td.nbmul = (td.L <= nb) ? 0 : uint64_t(double(nb) * 0x1p64 / double(td.L));
+  if (td.L > nb) {
+    const int bits = 64 - __clzll(td.L - 1);  // bit length of L - 1
+    td.bsh = bits > 32 ? uint32_t(bits - 32) : 0u;
+    const uint64_t Lp = ((td.L - 1) >> td.bsh) + 1;  // in (nb, 2^32]
+    td.bmul = uint32_t((uint64_t(nb) << 32) / Lp);
+  }
 }
 
 template <class Geom>
@@ -135,161 +153,230 @@ __global__ void __launch_bounds__(256)
 }
 
 struct FastSmem {
-  uint64_t A[K_MAX];          // draws scattered by bucket, then sorted in place;
-                              // with DIGEST the rows u afterwards
-  uint16_t hist[K_MAX + 2];   // bucket counts -> starts; per-draw codes in the rare path
+  uint64_t A[K_MAX];             // draws scattered by bucket, then sorted in place
+  uint64_t D[K_MAX];             // draws in draw order
+  uint32_t hist[NB_MAX / 2 + 1]; // packed 16-bit bucket counts -> starts (+ sentinel);
+                                 // per-draw 16-bit codes in the rare path
   uint32_t bitT[K_MAX / 32], bitJ[K_MAX / 32];
+  uint32_t multi[K_MAX / 2];     // buckets holding several values: start | count << 16
 };
+
+// Insertion sort of A[s0, s1) (one bucket, a handful of values); returns
+// whether two values are equal.
+__device__ __forceinline__ int sort_bucket(uint64_t* A, uint32_t s0, uint32_t s1) {
+  int dup = 0;
+  for (uint32_t i = s0 + 1; i < s1; ++i) {
+    const uint64_t v = A[i];
+    uint32_t j = i;
+    uint64_t y = A[j - 1];
+    while (y > v) {
+      A[j] = y;
+      --j;
+      if (j == s0) break;
+      y = A[j - 1];
+    }
+    dup |= (j > s0 && A[j - 1] == v);
+    A[j] = v;
+  }
+  return dup;
+}
 
 // TILE_SEED: every tile carries its own seed (batched instances); otherwise
 // the round keys of the one seed come in as a kernel parameter.
 template <class Geom, class Sink, bool DIGEST, bool TILE_SEED>
-__global__ void __launch_bounds__(FAST_THREADS, 5)
+__global__ void __launch_bounds__(FAST_THREADS, 4)
     leaf_fast_kernel(Geom g, Sink sink, int d, RoundKeys rk,
                      const TileDesc<typename Geom::Ctx>* __restrict__ desc, uint64_t ntiles,
                      int* err, DigestOut dig) {
-  __shared__ FastSmem sm;
+  __shared__ __align__(16) FastSmem sm;
   __shared__ unsigned bh[65];
   __shared__ unsigned long long red_d[FAST_THREADS / 32];
   __shared__ unsigned red_c1[FAST_THREADS / 32], red_nr[FAST_THREADS / 32];
   __shared__ uint64_t s_fu, s_lu;
   __shared__ uint32_t s_fl, s_ll;
+  __shared__ unsigned s_nmulti;
+  using Desc = TileDesc<typename Geom::Ctx>;
+  // the descriptors of this tile and the next one, staged in shared memory so
+  // that their fields are read where they are used instead of being held in
+  // registers for the whole tile
+  __shared__ __align__(16) Desc s_td[2];
   const int tid = threadIdx.x;
+  uint16_t* const st16 = reinterpret_cast<uint16_t*>(sm.hist);
+  auto stage = [&](uint64_t tt, int slot) {
+    static_assert(sizeof(Desc) % 4 == 0, "descriptor size");
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(desc + tt);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&s_td[slot]);
+    for (uint32_t w = tid; w < sizeof(Desc) / 4; w += FAST_THREADS) dst[w] = src[w];
+  };
 
-  for (uint32_t b = tid; b < (K_MAX + 2) / 2; b += FAST_THREADS)
-    reinterpret_cast<unsigned*>(sm.hist)[b] = 0;
+  for (uint32_t b = tid; b < NB_MAX / 2 + 1; b += FAST_THREADS) sm.hist[b] = 0;
+  if (blockIdx.x < ntiles) stage(blockIdx.x, 0);
   __syncthreads();
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const TileDesc<typename Geom::Ctx> td = desc[t];
-    if (td.flags != 0) continue;  // uniform over the block
-    const uint32_t k = td.k, nb = td.nb;
-    const uint64_t L = td.L, Lk = L - k, node = td.node(td.d, td.tau), nbmul = td.nbmul;
+  int cur = 0;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, cur ^= 1) {
+    const Desc& td = s_td[cur];
+    const uint64_t tn = t + gridDim.x;
+    if (td.flags != 0 || !sink.fits(td.base, td.k)) {  // uniform over the block
+      if (td.flags == 0 && tid == 0) set_error(err, ST_CAPACITY);  // the tile is dropped
+      if (tn < ntiles) stage(tn, cur ^ 1);
+      __syncthreads();
+      continue;
+    }
+    const uint32_t k = td.k, nb = td.nb, bsh = td.bsh, bmul = td.bmul;
+    const uint64_t Lk = td.L - k, node = td.node(td.d, td.tau);
     const uint64_t seed = td.seed;
 
-    // ---- 1./2. draws in registers, bucket counts and slots
-    uint64_t x[2 * FAST_PAIRS];
-    uint32_t slot[2 * FAST_PAIRS];
+    // ---- 1./2. draws, staged in D in draw order; bucket counts, and each
+    // draw's slot in its bucket (kept in registers)
+    uint32_t bs[2 * FAST_PAIRS];  // bucket | slot << 16
+    // Lemire's rejection test is done in the loop, the rejected draws (below
+    // L / 2^64 per draw) are redrawn after it, so that the retry code adds no
+    // live registers to the loop
+    uint32_t rejm = 0;
 #pragma unroll
     for (int s = 0; s < FAST_PAIRS; ++s) {
       const uint32_t i = 2 * (tid + FAST_THREADS * s);
-      if (i >= k) break;
-      uint32_t w[4];
-      if (TILE_SEED)
-        philox10(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, uint32_t(seed),
-                 uint32_t(seed >> 32), w);
-      else
-        philox10_rk(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, rk, w);
-      x[2 * s] = lemire_draw((uint64_t(w[0]) << 32) | w[1], Lk + i + 1, seed, node, i);
-      x[2 * s + 1] = (i + 1 < k)
-                         ? lemire_draw((uint64_t(w[2]) << 32) | w[3], Lk + i + 2, seed, node, i + 1)
-                         : 0;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (i + h < k) {
-          const uint64_t v = x[2 * s + h];
-          slot[2 * s + h] = bucket_of(v, nbmul, nb);
+      if (i < k) {
+        uint32_t w[4];
+        if (TILE_SEED)
+          philox10(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, uint32_t(seed),
+                   uint32_t(seed >> 32), w);
+        else
+          philox10_rk(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, rk, w);
+        const uint64_t a = (uint64_t(w[0]) << 32) | w[1], c = (uint64_t(w[2]) << 32) | w[3];
+        const uint64_t r0 = Lk + i + 1, r1 = r0 + 1;
+        const uint64_t x0 = mul_hi64(a, r0), x1 = mul_hi64(c, r1);
+        const bool ok0 = a * r0 >= r0, ok1 = c * r1 >= r1;
+        rejm |= (ok0 ? 0u : 1u << (2 * s)) | ((ok1 || i + 1 >= k) ? 0u : 2u << (2 * s));
+        if (ok0) {
+          const uint32_t b0 = bucket_of(x0, bsh, bmul);
+          const uint32_t sh0 = (b0 & 1) << 4;
+          const uint32_t old0 = atomicAdd(&sm.hist[b0 >> 1], 1u << sh0);
+          bs[2 * s] = b0 | (((old0 >> sh0) & 0xffffu) << 16);
         }
-      }
-    }
-    // bucket counts: 16-bit counters packed in pairs, updated with 32-bit atomics
-    unsigned* h32 = reinterpret_cast<unsigned*>(sm.hist);
-#pragma unroll
-    for (int s = 0; s < FAST_PAIRS; ++s) {
-      const uint32_t i = 2 * (tid + FAST_THREADS * s);
-      if (i >= k) break;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (i + h < k) {
-          const uint32_t b = slot[2 * s + h];
-          const unsigned old = atomicAdd(&h32[b >> 1], (b & 1) ? 0x10000u : 1u);
-          // keep bucket in the low 16 bits, the within-bucket slot above
-          slot[2 * s + h] = b | (((b & 1) ? (old >> 16) : (old & 0xffffu)) << 16);
-        }
-      }
-    }
-    __syncthreads();
-    // ---- 3. exclusive scan of hist[0..nb) in place, hist[nb] = k
-    {
-      const uint32_t per = (nb + FAST_THREADS - 1) / FAST_THREADS;
-      const uint32_t b0 = tid * per;
-      uint32_t s = 0;
-      for (uint32_t q = 0; q < per; ++q)
-        if (b0 + q < nb) s += sm.hist[b0 + q];
-      uint32_t tot;
-      uint32_t run = block_inclusive_scan<FAST_THREADS>(s, tot) - s;
-      for (uint32_t q = 0; q < per; ++q)
-        if (b0 + q < nb) {
-          const uint32_t c = sm.hist[b0 + q];
-          sm.hist[b0 + q] = uint16_t(run);
-          run += c;
-        }
-      if (tid == 0) sm.hist[nb] = uint16_t(k);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int s = 0; s < FAST_PAIRS; ++s) {
-      const uint32_t i = 2 * (tid + FAST_THREADS * s);
-      if (i >= k) break;
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-        if (i + h < k) {
-          const uint32_t b = slot[2 * s + h] & 0xffffu;
-          const uint32_t p = sm.hist[b] + (slot[2 * s + h] >> 16);
-          sm.A[p] = x[2 * s + h];
-          slot[2 * s + h] = b | (p << 16);  // bucket and scatter position
-        }
-    }
-    __syncthreads();
-    // ---- 4. rank inside the bucket (ties by scatter position); the rank lies
-    // in the bucket's own slot range, so after a barrier the values are
-    // written back in place
-    int dup = 0;
-    uint32_t rank[2 * FAST_PAIRS];
-#pragma unroll
-    for (int s = 0; s < FAST_PAIRS; ++s) {
-      const uint32_t i = 2 * (tid + FAST_THREADS * s);
-      if (i >= k) break;
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-        if (i + h < k) {
-          const uint64_t v = x[2 * s + h];
-          const uint32_t p = slot[2 * s + h] >> 16;
-          const uint32_t b = slot[2 * s + h] & 0xffffu;
-          const uint32_t s0 = sm.hist[b], s1 = sm.hist[b + 1];
-          uint32_t r = s0;
-          for (uint32_t q = s0; q < s1; ++q) {
-            const uint64_t y = sm.A[q];
-            r += (y < v) || (y == v && q < p);
-            dup |= (y == v && q != p);
+        if (i + 1 < k) {
+          if (ok1) {
+            const uint32_t b1 = bucket_of(x1, bsh, bmul);
+            const uint32_t sh1 = (b1 & 1) << 4;
+            const uint32_t old1 = atomicAdd(&sm.hist[b1 >> 1], 1u << sh1);
+            bs[2 * s + 1] = b1 | (((old1 >> sh1) & 0xffffu) << 16);
           }
-          rank[2 * s + h] = r;
+          reinterpret_cast<ulonglong2*>(sm.D)[i >> 1] = make_ulonglong2(x0, x1);
+        } else {
+          sm.D[i] = x0;
+        }
+      }
+    }
+    if (rejm) {
+#pragma unroll
+      for (int j = 0; j < 2 * FAST_PAIRS; ++j)
+        if (rejm & (1u << j)) {
+          const uint32_t i = 2 * (tid + FAST_THREADS * (j >> 1)) + (j & 1);
+          const uint64_t x = lemire_draw(stream_u64(seed, node, TAG_LEAF, i), Lk + i + 1, seed,
+                                         node, i);
+          const uint32_t b = bucket_of(x, bsh, bmul);
+          const uint32_t sh = (b & 1) << 4;
+          const uint32_t old = atomicAdd(&sm.hist[b >> 1], 1u << sh);
+          bs[j] = b | (((old >> sh) & 0xffffu) << 16);
+          sm.D[i] = x;
         }
     }
     __syncthreads();
+    // ---- 3. exclusive scan of the packed counts: thread tid owns words
+    // [tid*per, tid*per + per), per = nb / (2 FAST_THREADS) in {4, 8, ...}
+    {
+      const uint32_t per4 = nb / (8 * FAST_THREADS);  // uint4 groups per thread
+      uint4* h4 = reinterpret_cast<uint4*>(sm.hist) + tid * per4;
+      uint32_t sum = 0;
+      for (uint32_t q = 0; q < per4; ++q) {
+        const uint4 a = h4[q];
+        sum += (a.x & 0xffffu) + (a.x >> 16) + (a.y & 0xffffu) + (a.y >> 16) +
+               (a.z & 0xffffu) + (a.z >> 16) + (a.w & 0xffffu) + (a.w >> 16);
+      }
+      uint32_t tot;
+      uint32_t run = block_inclusive_scan<FAST_THREADS>(sum, tot) - sum;
+      for (uint32_t q = 0; q < per4; ++q) {
+        uint4 a = h4[q];
+        uint32_t c;
+        c = (a.x & 0xffffu) + (a.x >> 16); a.x = run * 0x10001u + (a.x << 16); run += c;
+        c = (a.y & 0xffffu) + (a.y >> 16); a.y = run * 0x10001u + (a.y << 16); run += c;
+        c = (a.z & 0xffffu) + (a.z >> 16); a.z = run * 0x10001u + (a.z << 16); run += c;
+        c = (a.w & 0xffffu) + (a.w >> 16); a.w = run * 0x10001u + (a.w << 16); run += c;
+        h4[q] = a;
+      }
+      if (tid == 0) {
+        sm.hist[nb >> 1] = k;  // start of the (absent) bucket nb
+        s_nmulti = 0;
+      }
+      if (DIGEST)
+        for (int b = tid; b < 65; b += FAST_THREADS) bh[b] = 0;
+    }
+    __syncthreads();  // bucket starts visible
+    // ---- 4. scatter D[i] to A[start(b) + slot] (the bucket's values land in
+    // [start(b), start(b+1)) in arbitrary order)
+    {
+      // the draw at slot 0 of a bucket with several values lists that bucket
+      // (warp-aggregated append), so that the sorting below runs over a
+      // compact list instead of diverging inside every warp
+      const int lane = tid & 31;
 #pragma unroll
-    for (int s = 0; s < FAST_PAIRS; ++s) {
-      const uint32_t i = 2 * (tid + FAST_THREADS * s);
-      if (i >= k) break;
+      for (int s = 0; s < FAST_PAIRS; ++s) {
+        const uint32_t i = 2 * (tid + FAST_THREADS * s);
 #pragma unroll
-      for (int h = 0; h < 2; ++h)
-        if (i + h < k) sm.A[rank[2 * s + h]] = x[2 * s + h];
+        for (int h = 0; h < 2; ++h) {
+          uint32_t item = 0;
+          if (i + h < k) {
+            const uint32_t v = bs[2 * s + h];
+            const uint32_t b = v & 0xffffu, s0 = st16[b];
+            sm.A[s0 + (v >> 16)] = sm.D[i + h];
+            if ((v >> 16) == 0) {
+              const uint32_t c = st16[b + 1] - s0;
+              if (c > 1) item = s0 | (c << 16);
+            }
+          }
+          if (2 * (FAST_THREADS * s) + h < k) {  // warp-uniform: some lane of the block is active
+            const unsigned m = __ballot_sync(0xffffffffu, item != 0);
+            if (m) {
+              unsigned at = 0;
+              if (lane == __ffs(m) - 1) at = atomicAdd(&s_nmulti, unsigned(__popc(m)));
+              at = __shfl_sync(0xffffffffu, at, __ffs(m) - 1);
+              if (item) sm.multi[at + __popc(m & ((1u << lane) - 1))] = item;
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+    // ---- 5. sort every listed bucket in place (mean occupancy <= 1/2: mostly
+    // pairs); equal values mean Floyd replaced a draw
+    int dup = 0;
+    const uint32_t nmulti = s_nmulti;
+    for (uint32_t e = tid; e < nmulti; e += FAST_THREADS) {
+      const uint32_t item = sm.multi[e];
+      const uint32_t s0 = item & 0xffffu, c = item >> 16;
+      if (c == 2) {
+        const uint64_t a = sm.A[s0], b = sm.A[s0 + 1];
+        if (b < a) {
+          sm.A[s0] = b;
+          sm.A[s0 + 1] = a;
+        }
+        dup |= (a == b);
+      } else {
+        dup |= sort_bucket(sm.A, s0, s0 + c);
+      }
     }
     const int any_dup = __syncthreads_or(dup);
     uint64_t* res = sm.A;
     if (any_dup) {
-      // ---- 5. sequential resolution in draw order.  A value v < L-k can only
+      // ---- 6. sequential resolution in draw order.  A value v < L-k can only
       // be taken by an earlier draw of v itself (first occurrence wins); the
       // values L-k .. L-1 are tracked in a bitmap because replacements land
       // there.  Per draw a 16-bit code: the first sorted position of v, or
       // 0x8000 | (v - (L-k)) for the top k values.
-#pragma unroll
-      for (int s = 0; s < FAST_PAIRS; ++s) {
-        const uint32_t i = 2 * (tid + FAST_THREADS * s);
-        if (i >= k) break;
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
+      for (uint32_t i = 2 * tid; i < k; i += 2 * FAST_THREADS) {
+        for (uint32_t h = 0; h < 2; ++h)
           if (i + h < k) {
-            const uint64_t v = x[2 * s + h];
+            const uint64_t v = sm.D[i + h];
             uint16_t code;
             if (v >= Lk) {
               code = uint16_t(0x8000u | uint32_t(v - Lk));
@@ -304,14 +391,14 @@ __global__ void __launch_bounds__(FAST_THREADS, 5)
               }
               code = uint16_t(a);
             }
-            sm.hist[i + h] = code;
+            st16[i + h] = code;
           }
       }
       for (uint32_t w = tid; w < K_MAX / 32; w += FAST_THREADS) sm.bitT[w] = sm.bitJ[w] = 0;
       __syncthreads();
       if (tid == 0) {
         for (uint32_t i = 0; i < k; ++i) {
-          const uint32_t code = sm.hist[i];
+          const uint32_t code = st16[i];
           if (!(code & 0x8000u)) {
             const uint32_t fp = code;
             if (sm.bitT[fp >> 5] & (1u << (fp & 31)))
@@ -346,44 +433,68 @@ __global__ void __launch_bounds__(FAST_THREADS, 5)
       }
       __syncthreads();
     }
-    // ---- 6. emit
+    // the bucket counters are dead from here on: clear them for the next tile
+    {
+      const uint32_t per4 = nb / (8 * FAST_THREADS);
+      uint4* h4 = reinterpret_cast<uint4*>(sm.hist) + tid * per4;
+      for (uint32_t q = 0; q < per4; ++q) h4[q] = make_uint4(0, 0, 0, 0);
+      if (tid == 0) sm.hist[nb >> 1] = 0;
+    }
+    // ---- 7. emit; lane l of warp w takes r = r0 + 32 w + l, so that every
+    // warp holds 32 consecutive sorted edges.  DIGEST: the order-independent
+    // digest, and the runs of equal rows u (A[r] is overwritten by u): a run
+    // starts where u differs from its predecessor, its length is the
+    // distance to the next start (ballot within the warp, a short scan of A
+    // past the warp's 32 edges otherwise).
     unsigned long long dsum = 0;
+    uint32_t c1 = 0, nr = 0;
     const uint64_t lo = td.lo, base = td.base;
     const typename Geom::Ctx gx = td.gx;
+    const int lane = tid & 31;
     for (uint32_t r = tid; r < k; r += FAST_THREADS) {
       uint64_t u, v;
       g.map(gx, lo + res[r], u, v);
-      sink.write(base + r, u, v);
+      sink.put(base + r, u, v);
       if (DIGEST) {
         dsum += edge_hash(u, v);
         res[r] = u;
       }
     }
     if (DIGEST) {
-      for (int b = tid; b < 65; b += FAST_THREADS) bh[b] = 0;
       __syncthreads();
-      uint32_t c1 = 0, nr = 0, fl = 0, ll = 0;
-      uint64_t fu = 0, lu = 0;
-      for (uint32_t r = tid; r < k; r += FAST_THREADS) {
-        const uint64_t u = res[r];
-        if (r > 0 && res[r - 1] == u) continue;
-        uint32_t len = 1;
-        while (r + len < k && res[r + len] == u) ++len;
-        ++nr;
-        const bool first = (r == 0), last = (r + len == k);
-        if (first) {
-          fu = u;
-          fl = len;
-        }
-        if (last) {
-          lu = u;
-          ll = len;
-        }
-        if (!first && !last) {
-          if (len == 1)
-            ++c1;
-          else
-            atomicAdd(&bh[len < 64 ? len : 64], 1u);
+      for (uint32_t r0 = 0; r0 < k; r0 += FAST_THREADS) {  // uniform over the block
+        const uint32_t r = r0 + tid;
+        const uint64_t u = r < k ? res[r] : ~uint64_t(0);
+        uint64_t prev = __shfl_up_sync(0xffffffffu, u, 1);
+        if (lane == 0) prev = (r > 0 && r < k) ? res[r - 1] : ~uint64_t(0);
+        const bool st = r < k && u != prev;
+        const unsigned m = __ballot_sync(0xffffffffu, st);
+        if (st) {
+          const unsigned later = lane == 31 ? 0u : (m >> (lane + 1));
+          uint32_t len;
+          if (later) {
+            len = __ffs(later);
+          } else {  // the run reaches past this warp's edges
+            uint32_t q = r + 1;
+            while (q < k && res[q] == u) ++q;
+            len = q - r;
+          }
+          ++nr;
+          const bool first = (r == 0), last = (r + len == k);
+          if (first) {
+            s_fu = u;
+            s_fl = len;
+          }
+          if (last) {
+            s_lu = u;
+            s_ll = len;
+          }
+          if (!first && !last) {
+            if (len == 1)
+              ++c1;
+            else
+              atomicAdd(&bh[len < 64 ? len : 64], 1u);
+          }
         }
       }
       // block totals (FAST_THREADS threads)
@@ -393,19 +504,11 @@ __global__ void __launch_bounds__(FAST_THREADS, 5)
         c1 += __shfl_xor_sync(0xffffffffu, c1, o);
         nr += __shfl_xor_sync(0xffffffffu, nr, o);
       }
-      const int lane = tid & 31, wid = tid >> 5;
+      const int wid = tid >> 5;
       if (lane == 0) {
         red_d[wid] = dsum;
         red_c1[wid] = c1;
         red_nr[wid] = nr;
-      }
-      if (fl) {
-        s_fu = fu;
-        s_fl = fl;
-      }
-      if (ll) {
-        s_lu = lu;
-        s_ll = ll;
       }
       __syncthreads();
       const uint64_t cl = t >> d;
@@ -431,10 +534,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 5)
       for (int b = tid; b < 65; b += FAST_THREADS)
         if (bh[b]) atomicAdd(&dig.hist[cl * 65 + b], (unsigned long long)bh[b]);
     }
-    // clear the bucket counters for the next tile (all of them: the rare path
-    // reuses the array)
-    for (uint32_t b = tid; b < (K_MAX + 2) / 2; b += FAST_THREADS)
-      reinterpret_cast<unsigned*>(sm.hist)[b] = 0;
+    if (tn < ntiles) stage(tn, cur ^ 1);
     __syncthreads();
   }
 }

@@ -45,6 +45,10 @@ CASES = [
     ((1 << 33) + 5, 1 << 20, 19, 17, 8, 1024, 2048),  # universe > 2^64: binomial regime, fair bits
     (4097, 300000, 23, 4097, 4, 64, 100),          # one row per chunk
     (600, 5000, 29, 600, 4, 3, 5),                 # many tiny tiles with re-splits
+    (3037000501, 1000, 31, 1, 4, 1024, 2048),      # one tile just above 2^63 pairs: Lemire
+                                                   # rejects about half of the draws
+    (1 << 32, 1500, 37, 1, 8, 1024, 2048),         # one tile near 2^64: every draw takes the
+                                                   # rejection test's slow branch
 ]
 
 
