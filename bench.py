@@ -134,6 +134,29 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def replica_seed(rank):
+    """Seed of the replica on `rank`: the ranks generate independent graphs of
+    the same workload (the path shards with no data exchange)."""
+    return SEED + rank
+
+
+def max_over_ranks(x, device, world):
+    """The largest value of x over all ranks (the slowest rank's time)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank_step, steps, world, seconds):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time."""
+    return units_per_rank_step * steps * world / seconds
+
+
 def _timed(fn, reps, warm=2):
     """Median milliseconds of fn() over reps runs (CUDA events, current stream)."""
     import torch
@@ -295,7 +318,7 @@ def main():
         if world > 1:
             dist.barrier()
 
-    seed = SEED + rank  # independent replicas (weak scaling, no data-path collective)
+    seed = replica_seed(rank)  # independent replicas (weak scaling, no data-path collective)
     dev = torch.device("cuda", local)
     main = torch.cuda.current_stream()
     s = main.cuda_stream
@@ -353,10 +376,7 @@ def main():
     rows = N_VERT // P_CHUNKS
     if tot != M_EDGES or int(hist[:16].sum()) != 16 * rows:
         raise RuntimeError("inconsistent chunk counts or histogram")
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dev, world)
 
     # end to end through the public entry points with host result buffers:
     # per step the per-chunk digests and histograms go to pinned host memory
@@ -371,14 +391,10 @@ def main():
         h_hist.copy_(hist, non_blocking=True)
         kg.check_device_error()  # synchronises the stream
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dev, world)
 
-    total_edges = M_EDGES * args.steps * world
-    value = total_edges / (ms / 1e3)
-    e2e = total_edges / e2e_s
+    value = aggregate_rate(M_EDGES, args.steps, world, ms / 1e3)
+    e2e = aggregate_rate(M_EDGES, args.steps, world, e2e_s)
     peak, peak_kind = peaks()
     leaf_ms, leaf_n = prof["leaf"]
     per_launch_s = leaf_ms / 1e3 / max(leaf_n, 1)
