@@ -40,14 +40,11 @@ struct BatchGeom {
       u = x.r0 + q;
       v = w + (w >= u ? 1 : 0);
     } else if (x.kind == 1) {
-      const uint64_t q = off / x.sj;
+      const uint64_t q = rect_row(off, x.sj);
       u = x.ri + q;
       v = x.rj + (off - q * x.sj);
     } else {
-      uint64_t w = uint64_t((1.0 + sqrt(1.0 + 8.0 * double(off))) * 0.5);
-      if (w < 1) w = 1;
-      while (u128(w) * (w - 1) / 2 > off) --w;
-      while (u128(w + 1) * w / 2 <= off) ++w;
+      const uint64_t w = tri_row(off);
       u = x.ri + w;
       v = x.ri + (off - uint64_t(u128(w) * (w - 1) / 2));
     }
@@ -381,7 +378,7 @@ __global__ void batch_und_scatter(const BInst* __restrict__ inst, uint32_t count
   }
 }
 
-// Rows of <= 32 entries sorted by one warp (bitonic across lanes); longer rows listed.
+// Rows of <= WARP_SORT_MAX entries sorted by one warp; longer rows listed.
 __global__ void __launch_bounds__(256)
     batch_und_sort_short(uint64_t nverts, const unsigned long long* __restrict__ rowpos,
                          const unsigned long long* __restrict__ deg, uint32_t* __restrict__ out,
@@ -391,24 +388,12 @@ __global__ void __launch_bounds__(256)
   const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
   for (uint64_t r = warp; r < nverts; r += nwarps) {
     const uint64_t b = rowpos[r], dg = deg[r];
-    if (dg == 0 || b + dg > cap) continue;
-    if (dg > 32) {
+    if (dg <= 1 || b + dg > cap) continue;
+    if (dg > WARP_SORT_MAX) {
       if (lane == 0) long_rows[atomicAdd(nlong, 1ull)] = r;
       continue;
     }
-    uint64_t x = lane < dg ? uint64_t(out[2 * (b + lane) + 1]) : ~uint64_t(0);
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        const uint64_t y = __shfl_xor_sync(0xffffffffu, x, j);
-        const bool up = ((lane & k) == 0);
-        const bool lower = ((lane & j) == 0);
-        const uint64_t mn = x < y ? x : y, mx = x < y ? y : x;
-        x = (lower == up) ? mn : mx;
-      }
-    }
-    if (lane < dg) out[2 * (b + lane) + 1] = uint32_t(x);
+    warp_sort_row(out, b, dg, lane);
   }
 }
 
@@ -423,7 +408,11 @@ __global__ void __launch_bounds__(256)
     const uint64_t r = long_rows[q];
     const uint64_t b = rowpos[r], n = deg[r];
     uint64_t N = 1;
-    while (N < n) N <<= 1;
+    int lgN = 0;
+    while (N < n) {
+      N <<= 1;
+      ++lgN;
+    }
     const bool in_smem = n <= LONG_SMEM;
     if (in_smem)
       for (uint64_t i = threadIdx.x; i < n; i += blockDim.x) sh[i] = out[2 * (b + i) + 1];
@@ -435,9 +424,10 @@ __global__ void __launch_bounds__(256)
       else
         out[2 * (b + i) + 1] = uint32_t(x);
     };
-    for (uint64_t k = 2; k <= N; k <<= 1) {
+    for (int lk = 1; lk <= lgN; ++lk) {
+      const uint64_t k = uint64_t(1) << lk;
       for (uint64_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
-        const uint64_t blk = i / (k / 2), off = i % (k / 2);
+        const uint64_t blk = i >> (lk - 1), off = i & (k / 2 - 1);
         const uint64_t lo = blk * k + off, hi = blk * k + k - 1 - off;
         if (hi < n) {
           const uint64_t x = get(lo), y = get(hi);
@@ -448,9 +438,10 @@ __global__ void __launch_bounds__(256)
         }
       }
       __syncthreads();
-      for (uint64_t j = k / 4; j >= 1; j >>= 1) {
+      for (int lj = lk - 2; lj >= 0; --lj) {
+        const uint64_t j = uint64_t(1) << lj;
         for (uint64_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
-          const uint64_t blk = i / j, off = i % j;
+          const uint64_t blk = i >> lj, off = i & (j - 1);
           const uint64_t lo = blk * 2 * j + off, hi = lo + j;
           if (hi < n) {
             const uint64_t x = get(lo), y = get(hi);

@@ -71,6 +71,32 @@ struct DirGeom {
   }
 };
 
+// Row of offset `off` in a rectangle of row length sj: off / sj, in 32-bit
+// arithmetic when both fit (the common case), else 64-bit.
+__host__ __device__ __forceinline__ uint64_t rect_row(uint64_t off, uint64_t sj) {
+  if ((off | sj) <= 0xffffffffull) return uint32_t(off) / uint32_t(sj);
+  return off / sj;
+}
+
+// Largest w >= 1 with w (w - 1) / 2 <= off (the row of a triangle offset):
+// a square-root estimate (single precision below 2^40, double above),
+// corrected exactly in integers.
+__host__ __device__ __forceinline__ uint64_t tri_row(uint64_t off) {
+  uint64_t w;
+  if (off < (uint64_t(1) << 40)) {
+    w = uint64_t((1.0f + sqrtf(1.0f + 8.0f * float(off))) * 0.5f);
+    if (w < 1) w = 1;
+    while (w * (w - 1) / 2 > off) --w;
+    while ((w + 1) * w / 2 <= off) ++w;
+    return w;
+  }
+  w = uint64_t((1.0 + sqrt(1.0 + 8.0 * double(off))) * 0.5);
+  if (w < 1) w = 1;
+  while (u128(w) * (w - 1) / 2 > off) --w;
+  while (u128(w + 1) * w / 2 <= off) ++w;
+  return w;
+}
+
 // Undirected chunks (Sec. 4.2): chunk (i, j), j <= i, of the triangular P x P
 // chunk matrix; chunk index k enumerates (i, j) row by row, k = i(i+1)/2 + j,
 // and the chunk's stream id is i P + j.  Rectangles (i > j) are row-major,
@@ -123,16 +149,12 @@ struct UndGeom {
   __host__ __device__ __forceinline__ void map(const Ctx& x, uint64_t off, uint64_t& u,
                                                uint64_t& v) const {
     if (!x.tri) {
-      const uint64_t q = off / x.sj;
+      const uint64_t q = rect_row(off, x.sj);
       u = x.ri + q;
       v = x.rj + (off - q * x.sj);
       return;
     }
-    // largest w with w(w-1)/2 <= off, from the square root, then corrected
-    uint64_t w = uint64_t((1.0 + sqrt(1.0 + 8.0 * double(off))) * 0.5);
-    if (w < 1) w = 1;
-    while (u128(w) * (w - 1) / 2 > off) --w;
-    while (u128(w + 1) * w / 2 <= off) ++w;
+    const uint64_t w = tri_row(off);
     u = x.ri + w;
     v = x.ri + (off - uint64_t(u128(w) * (w - 1) / 2));
   }

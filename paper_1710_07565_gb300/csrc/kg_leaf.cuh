@@ -361,6 +361,24 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
           sm.A[s0 + 1] = a;
         }
         dup |= (a == b);
+      } else if (c <= 4) {  // four loads at once, a 5-exchange network, c stores
+        uint64_t y[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) y[q] = uint32_t(q) < c ? sm.A[s0 + q] : ~uint64_t(0);
+        auto cx = [](uint64_t& a, uint64_t& b) {
+          const uint64_t lo_ = a < b ? a : b, hi_ = a < b ? b : a;
+          a = lo_;
+          b = hi_;
+        };
+        cx(y[0], y[1]);
+        cx(y[2], y[3]);
+        cx(y[0], y[2]);
+        cx(y[1], y[3]);
+        cx(y[1], y[2]);
+        dup |= (y[0] == y[1]) | (y[1] == y[2] && c > 2) | (y[2] == y[3] && c > 3);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (uint32_t(q) < c) sm.A[s0 + q] = y[q];
       } else {
         dup |= sort_bucket(sm.A, s0, s0 + c);
       }
@@ -443,9 +461,9 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
     // ---- 7. emit; lane l of warp w takes r = r0 + 32 w + l, so that every
     // warp holds 32 consecutive sorted edges.  DIGEST: the order-independent
     // digest, and the runs of equal rows u (A[r] is overwritten by u): a run
-    // starts where u differs from its predecessor, its length is the
-    // distance to the next start (ballot within the warp, a short scan of A
-    // past the warp's 32 edges otherwise).
+    // starts where u differs from its predecessor (neighbours by warp
+    // shuffles, A across warps); a run longer than one is measured by a scan
+    // of A from its start.
     unsigned long long dsum = 0;
     uint32_t c1 = 0, nr = 0;
     const uint64_t lo = td.lo, base = td.base;
@@ -464,18 +482,16 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
       __syncthreads();
       for (uint32_t r0 = 0; r0 < k; r0 += FAST_THREADS) {  // uniform over the block
         const uint32_t r = r0 + tid;
-        const uint64_t u = r < k ? res[r] : ~uint64_t(0);
+        const bool in = r < k;
+        const uint64_t u = in ? res[r] : ~uint64_t(0) - 1;
         uint64_t prev = __shfl_up_sync(0xffffffffu, u, 1);
-        if (lane == 0) prev = (r > 0 && r < k) ? res[r - 1] : ~uint64_t(0);
-        const bool st = r < k && u != prev;
-        const unsigned m = __ballot_sync(0xffffffffu, st);
-        if (st) {
-          const unsigned later = lane == 31 ? 0u : (m >> (lane + 1));
-          uint32_t len;
-          if (later) {
-            len = __ffs(later);
-          } else {  // the run reaches past this warp's edges
-            uint32_t q = r + 1;
+        uint64_t next = __shfl_down_sync(0xffffffffu, u, 1);
+        if (lane == 0) prev = (in && r > 0) ? res[r - 1] : ~uint64_t(0);
+        if (lane == 31) next = (r + 1 < k) ? res[r + 1] : ~uint64_t(0);
+        if (in && (r == 0 || u != prev)) {  // a run of rows u starts at r
+          uint32_t len = 1;
+          if (r + 1 < k && u == next) {
+            uint32_t q = r + 2;
             while (q < k && res[q] == u) ++q;
             len = q - r;
           }

@@ -171,8 +171,75 @@ __global__ void und_scatter(const Id* __restrict__ pairs, const uint64_t* __rest
   }
 }
 
-// Rows of at most 32 entries: one warp per row, bitonic sort across the lanes.
-// Longer rows are listed for und_sort_long.
+// Bitonic sort of 32 E values held by one warp, E consecutive values per lane
+// (value index = lane E + e): exchanges at distance j < E stay in the lane,
+// longer ones go through shuffles.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(uint64_t (&x)[E], unsigned lane) {
+#pragma unroll
+  for (int k = 2; k <= 32 * E; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      if (j >= E) {
+        const int lj = j / E;
+        const bool lower = (lane & lj) == 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const bool up = ((lane * E + e) & k) == 0;
+          const uint64_t y = __shfl_xor_sync(0xffffffffu, x[e], lj);
+          const uint64_t mn = x[e] < y ? x[e] : y, mx = x[e] < y ? y : x[e];
+          x[e] = (lower == up) ? mn : mx;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int q = e ^ j;
+          if (q > e) {
+            const bool up = ((lane * E + e) & k) == 0;
+            const uint64_t a = x[e], b = x[q];
+            const bool sw = up ? (b < a) : (a < b);
+            x[e] = sw ? b : a;
+            x[q] = sw ? a : b;
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int E, class Id>
+__device__ __forceinline__ void warp_sort_row_e(Id* out, uint64_t b, uint64_t deg, unsigned lane) {
+  uint64_t x[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint64_t i = lane * E + e;
+    x[e] = i < deg ? uint64_t(out[2 * (b + i) + 1]) : ~uint64_t(0);
+  }
+  warp_bitonic<E>(x, lane);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint64_t i = lane * E + e;
+    if (i < deg) out[2 * (b + i) + 1] = Id(x[e]);
+  }
+}
+
+constexpr uint64_t WARP_SORT_MAX = 256;
+
+// Sorts the second ids of row entries [b, b + deg) by one warp (deg <= 256).
+template <class Id>
+__device__ __forceinline__ void warp_sort_row(Id* out, uint64_t b, uint64_t deg, unsigned lane) {
+  if (deg <= 32)
+    warp_sort_row_e<1>(out, b, deg, lane);
+  else if (deg <= 64)
+    warp_sort_row_e<2>(out, b, deg, lane);
+  else if (deg <= 128)
+    warp_sort_row_e<4>(out, b, deg, lane);
+  else
+    warp_sort_row_e<8>(out, b, deg, lane);
+}
+
+// Rows of at most WARP_SORT_MAX entries: one warp per row.  Longer rows are
+// listed for und_sort_long.
 template <class Id>
 __global__ void __launch_bounds__(256)
     und_sort_short(const uint64_t* __restrict__ rowptr, uint64_t n, Id* __restrict__ out,
@@ -182,25 +249,13 @@ __global__ void __launch_bounds__(256)
   const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
   for (uint64_t u = warp; u < n; u += nwarps) {
     const uint64_t b = rowptr[u], e = rowptr[u + 1] < cap ? rowptr[u + 1] : cap;
-    if (e <= b) continue;
+    if (e <= b + 1) continue;
     const uint64_t deg = e - b;
-    if (deg > 32) {
+    if (deg > WARP_SORT_MAX) {
       if (lane == 0) long_rows[atomicAdd(nlong, 1ull)] = u;
       continue;
     }
-    uint64_t x = lane < deg ? uint64_t(out[2 * (b + lane) + 1]) : ~uint64_t(0);
-#pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
-#pragma unroll
-      for (int j = k >> 1; j > 0; j >>= 1) {
-        const uint64_t y = __shfl_xor_sync(0xffffffffu, x, j);
-        const bool up = ((lane & k) == 0);
-        const bool lower = ((lane & j) == 0);
-        const uint64_t mn = x < y ? x : y, mx = x < y ? y : x;
-        x = (lower == up) ? mn : mx;
-      }
-    }
-    if (lane < deg) out[2 * (b + lane) + 1] = Id(x);
+    warp_sort_row(out, b, deg, lane);
   }
 }
 
@@ -223,7 +278,11 @@ __global__ void __launch_bounds__(256)
     const uint64_t b = rowptr[u], e = rowptr[u + 1] < cap ? rowptr[u + 1] : cap;
     const uint64_t deg = e - b;
     uint64_t N = 1;
-    while (N < deg) N <<= 1;
+    int lgN = 0;
+    while (N < deg) {
+      N <<= 1;
+      ++lgN;
+    }
     const bool in_smem = deg <= LONG_SMEM;
     if (in_smem)
       for (uint64_t i = threadIdx.x; i < deg; i += blockDim.x) sh[i] = out[2 * (b + i) + 1];
@@ -235,9 +294,10 @@ __global__ void __launch_bounds__(256)
       else
         out[2 * (b + i) + 1] = Id(x);
     };
-    for (uint64_t k = 2; k <= N; k <<= 1) {
+    for (int lk = 1; lk <= lgN; ++lk) {
+      const uint64_t k = uint64_t(1) << lk;
       for (uint64_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
-        const uint64_t blk = i / (k / 2), off = i % (k / 2);
+        const uint64_t blk = i >> (lk - 1), off = i & (k / 2 - 1);
         const uint64_t lo = blk * k + off, hi = blk * k + k - 1 - off;
         if (hi < deg) {
           const uint64_t x = get(lo), y = get(hi);
@@ -248,9 +308,10 @@ __global__ void __launch_bounds__(256)
         }
       }
       __syncthreads();
-      for (uint64_t j = k / 4; j >= 1; j >>= 1) {
+      for (int lj = lk - 2; lj >= 0; --lj) {
+        const uint64_t j = uint64_t(1) << lj;
         for (uint64_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
-          const uint64_t blk = i / j, off = i % j;
+          const uint64_t blk = i >> lj, off = i & (j - 1);
           const uint64_t lo = blk * 2 * j + off, hi = lo + j;
           if (hi < deg) {
             const uint64_t x = get(lo), y = get(hi);
