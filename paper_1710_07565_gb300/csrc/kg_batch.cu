@@ -115,6 +115,23 @@ __device__ __forceinline__ uint32_t find_inst(const BInst* __restrict__ inst, ui
   return a;
 }
 
+// find_inst for 32 consecutive positions p (lane l holds p0 + l; every lane
+// of the warp calls it): one search by lane 0, and a search of its own only
+// for a lane past the next instance's start.
+__device__ __forceinline__ uint32_t warp_find_inst(const BInst* __restrict__ inst, uint32_t count,
+                                                   uint64_t p, int which, unsigned lane) {
+  const uint64_t p0 = __shfl_sync(0xffffffffu, p, 0);
+  uint32_t i0 = 0;
+  if (lane == 0) i0 = find_inst(inst, count, p0, which);
+  i0 = __shfl_sync(0xffffffffu, i0, 0);
+  uint64_t nxt = ~uint64_t(0);
+  if (i0 + 1 < count)
+    nxt = which == 0 ? inst[i0 + 1].tile_base
+          : which == 1 ? inst[i0 + 1].pair_base
+                       : inst[i0 + 1].vert_base;
+  return p < nxt ? i0 : find_inst(inst, count, p, which);
+}
+
 __device__ __forceinline__ uint64_t b_universe(const BInst& I, uint64_t c) {
   if (!I.undirected) return (I.rb(c + 1) - I.rb(c)) * (I.n - 1);
   uint32_t i, j;
@@ -338,11 +355,15 @@ __global__ void __launch_bounds__(256)
 __global__ void batch_und_degree(const BInst* __restrict__ inst, uint32_t count, uint64_t npairs,
                                  const uint32_t* __restrict__ pairs,
                                  unsigned long long* __restrict__ deg) {
-  for (uint64_t p = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < npairs;
-       p += uint64_t(gridDim.x) * blockDim.x) {
-    const BInst& I = inst[find_inst(inst, count, p, 1)];
-    atomicAdd(&deg[I.vert_base + pairs[2 * p]], 1ull);
-    atomicAdd(&deg[I.vert_base + pairs[2 * p + 1]], 1ull);
+  const unsigned lane = threadIdx.x & 31;
+  for (uint64_t p0 = uint64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); p0 < npairs;
+       p0 += uint64_t(gridDim.x) * blockDim.x) {  // uniform over the warp
+    const uint64_t p = p0 + lane;
+    const uint64_t vb = inst[warp_find_inst(inst, count, p < npairs ? p : npairs - 1, 1, lane)].vert_base;
+    if (p < npairs) {
+      atomicAdd(&deg[vb + pairs[2 * p]], 1ull);
+      atomicAdd(&deg[vb + pairs[2 * p + 1]], 1ull);
+    }
   }
 }
 
@@ -361,12 +382,15 @@ __global__ void batch_und_scatter(const BInst* __restrict__ inst, uint32_t count
                                   const uint32_t* __restrict__ pairs,
                                   unsigned long long* __restrict__ cursor,
                                   uint32_t* __restrict__ out, uint64_t cap, int* err) {
-  for (uint64_t p = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < npairs;
-       p += uint64_t(gridDim.x) * blockDim.x) {
-    const BInst& I = inst[find_inst(inst, count, p, 1)];
+  const unsigned lane = threadIdx.x & 31;
+  for (uint64_t p0 = uint64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); p0 < npairs;
+       p0 += uint64_t(gridDim.x) * blockDim.x) {  // uniform over the warp
+    const uint64_t p = p0 + lane;
+    const uint64_t vb = inst[warp_find_inst(inst, count, p < npairs ? p : npairs - 1, 1, lane)].vert_base;
+    if (p >= npairs) continue;
     const uint32_t u = pairs[2 * p], v = pairs[2 * p + 1];
-    const uint64_t a = atomicAdd(&cursor[I.vert_base + u], 1ull);
-    const uint64_t b = atomicAdd(&cursor[I.vert_base + v], 1ull);
+    const uint64_t a = atomicAdd(&cursor[vb + u], 1ull);
+    const uint64_t b = atomicAdd(&cursor[vb + v], 1ull);
     if (a < cap && b < cap) {
       out[2 * a] = u;
       out[2 * a + 1] = v;

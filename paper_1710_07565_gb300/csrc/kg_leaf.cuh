@@ -386,69 +386,100 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
     const int any_dup = __syncthreads_or(dup);
     uint64_t* res = sm.A;
     if (any_dup) {
-      // ---- 6. sequential resolution in draw order.  A value v < L-k can only
-      // be taken by an earlier draw of v itself (first occurrence wins); the
-      // values L-k .. L-1 are tracked in a bitmap because replacements land
-      // there.  Per draw a 16-bit code: the first sorted position of v, or
-      // 0x8000 | (v - (L-k)) for the top k values.
-      for (uint32_t i = 2 * tid; i < k; i += 2 * FAST_THREADS) {
-        for (uint32_t h = 0; h < 2; ++h)
-          if (i + h < k) {
-            const uint64_t v = sm.D[i + h];
-            uint16_t code;
-            if (v >= Lk) {
-              code = uint16_t(0x8000u | uint32_t(v - Lk));
-            } else {
-              uint32_t a = 0, e = k;
-              while (a < e) {
-                const uint32_t mid = (a + e) >> 1;
-                if (sm.A[mid] < v)
-                  a = mid + 1;
-                else
-                  e = mid;
-              }
-              code = uint16_t(a);
-            }
-            st16[i + h] = code;
-          }
-      }
+      // ---- 6. Floyd's replacements, resolved in parallel.  Draw i inserts
+      // t_i unless t_i is already taken, else j_i = L-k+i (never taken
+      // before step i).  A value below L-k can only be taken by a draw of
+      // itself, so there the first draw of the value (in draw order) keeps
+      // it and later ones are replaced.  A value v >= L-k is also the
+      // replacement of draw p = v-(L-k) <= i: its first draw keeps it
+      // exactly when draw p kept its own value (p = i: always), which chains
+      // through earlier draws and is settled in rounds.  The kept values
+      // below L-k are then compacted in sorted order, followed by the taken
+      // values of [L-k, L) from a bitmap.
+      uint32_t* first = sm.hist;                                   // per sorted position
+      volatile uint8_t* status = reinterpret_cast<uint8_t*>(sm.multi);  // per draw: 0 keep,
+                                                                   // 1 replaced, 2 open
+      for (uint32_t r = tid; r < k; r += FAST_THREADS) first[r] = 0xffffffffu;
       for (uint32_t w = tid; w < K_MAX / 32; w += FAST_THREADS) sm.bitT[w] = sm.bitJ[w] = 0;
       __syncthreads();
-      if (tid == 0) {
-        for (uint32_t i = 0; i < k; ++i) {
-          const uint32_t code = st16[i];
-          if (!(code & 0x8000u)) {
-            const uint32_t fp = code;
-            if (sm.bitT[fp >> 5] & (1u << (fp & 31)))
-              sm.bitJ[i >> 5] |= 1u << (i & 31);
-            else
-              sm.bitT[fp >> 5] |= 1u << (fp & 31);
-          } else {
-            const uint32_t bj = code & 0x7fffu;
-            if (sm.bitJ[bj >> 5] & (1u << (bj & 31)))
-              sm.bitJ[i >> 5] |= 1u << (i & 31);
-            else
-              sm.bitJ[bj >> 5] |= 1u << (bj & 31);
-          }
+      auto first_pos = [&](uint64_t v) {  // first sorted position of v
+        uint32_t a = 0, e = k;
+        while (a < e) {
+          const uint32_t mid = (a + e) >> 1;
+          if (sm.A[mid] < v)
+            a = mid + 1;
+          else
+            e = mid;
         }
-        // the taken set in increasing order, compacted in place (the write
-        // index never passes the read index)
-        uint32_t o = 0;
-        uint64_t prev = 0;
-        for (uint32_t r = 0; r < k; ++r) {
-          const uint64_t v = sm.A[r];
-          if (v >= Lk) break;
-          const bool first = (r == 0 || prev != v);
-          prev = v;
-          if (first && (sm.bitT[r >> 5] & (1u << (r & 31)))) sm.A[o++] = v;
-        }
-        for (uint32_t bj = 0; bj < k; ++bj)
-          if (sm.bitJ[bj >> 5] & (1u << (bj & 31))) {
-            if (o < k) sm.A[o] = Lk + bj;
-            ++o;
-          }
-        if (o != k) set_error(err, ST_INTERNAL);
+        return a;
+      };
+      for (uint32_t i = tid; i < k; i += FAST_THREADS) atomicMin(&first[first_pos(sm.D[i])], i);
+      __syncthreads();
+      for (uint32_t i = tid; i < k; i += FAST_THREADS) {
+        const uint64_t v = sm.D[i];
+        const bool is_first = first[first_pos(v)] == i;
+        uint8_t st;
+        if (!is_first)
+          st = 1;
+        else if (v < Lk || v - Lk == i)
+          st = 0;
+        else
+          st = 2;
+        status[i] = st;
       }
+      __syncthreads();
+      for (;;) {
+        int open = 0;
+        for (uint32_t i = tid; i < k; i += FAST_THREADS)
+          if (status[i] == 2) {
+            const uint8_t sp = status[uint32_t(sm.D[i] - Lk)];
+            if (sp != 2)
+              status[i] = sp;
+            else
+              open = 1;
+          }
+        if (!__syncthreads_or(open)) break;
+      }
+      for (uint32_t i = tid; i < k; i += FAST_THREADS) {
+        const uint64_t v = sm.D[i];
+        if (status[i]) {
+          atomicOr(&sm.bitJ[i >> 5], 1u << (i & 31));  // j_i = L-k+i
+        } else if (v >= Lk) {
+          const uint32_t b = uint32_t(v - Lk);
+          atomicOr(&sm.bitJ[b >> 5], 1u << (b & 31));
+        } else {
+          const uint32_t fp = first_pos(v);
+          atomicOr(&sm.bitT[fp >> 5], 1u << (fp & 31));
+        }
+      }
+      __syncthreads();
+      // compaction into D: kept values below L-k (marked sorted positions),
+      // then L-k + b for the marked b; word counts scanned by the block
+      const uint32_t nw = (k + 31) >> 5;
+      uint32_t cT = 0, cJ = 0;
+      if (tid < nw) {
+        cT = __popc(sm.bitT[tid]);
+        cJ = __popc(sm.bitJ[tid]);
+      }
+      uint32_t totT, totJ;
+      const uint32_t offT = block_inclusive_scan<FAST_THREADS>(cT, totT) - cT;
+      const uint32_t offJ = block_inclusive_scan<FAST_THREADS>(cJ, totJ) - cJ;
+      if (tid < nw) {
+        uint32_t wT = sm.bitT[tid], wJ = sm.bitJ[tid], oT = offT, oJ = totT + offJ;
+        while (wT) {
+          const int b = __ffs(wT) - 1;
+          wT &= wT - 1;
+          sm.D[oT++] = sm.A[tid * 32 + b];
+        }
+        while (wJ) {
+          const int b = __ffs(wJ) - 1;
+          wJ &= wJ - 1;
+          if (oJ < k) sm.D[oJ] = Lk + tid * 32 + b;
+          ++oJ;
+        }
+      }
+      if (tid == 0 && totT + totJ != k) set_error(err, ST_INTERNAL);
+      res = sm.D;
       __syncthreads();
     }
     // the bucket counters are dead from here on: clear them for the next tile
