@@ -95,6 +95,10 @@ def lib():
             L.or_gnm_undirected.restype = i32
             L.or_gnp.argtypes = [i32, u64, dbl, u64, u32, u32, p64, p64, u64, p64]
             L.or_gnp.restype = i32
+            L.or_gnp_binomial_counts.argtypes = [i32, u64, dbl, u64, u32, p64]
+            L.or_gnp_binomial_counts.restype = i32
+            L.or_gnp_binomial.argtypes = [i32, u64, dbl, u64, u32, u32, u32, p64, p64, u64, p64]
+            L.or_gnp_binomial.restype = i32
             L.or_edge_checksum.argtypes = [p64, p64, u64]
             L.or_edge_checksum.restype = u64
             L.or_outdegree_hist.argtypes = [p64, u64, u64, u64, p64]
@@ -227,6 +231,32 @@ def gnp(undirected, n, p, seed, P, k_leaf=K_LEAF, cap_hint=None):
             cap = cnt.value
             continue
         _check(rc, "gnp")
+        return u[:cnt.value], v[:cnt.value]
+
+
+def gnp_binomial_counts(undirected, n, p, seed, P):
+    """Sec. 4.3 chunk counts: P (directed) or P(P+1)/2 (undirected) binomials."""
+    C = P * (P + 1) // 2 if undirected else P
+    cnt = np.zeros(C, dtype=np.uint64)
+    _check(lib().or_gnp_binomial_counts(1 if undirected else 0, n, p, seed, P, _p64(cnt)),
+           "gnp_binomial_counts")
+    return cnt
+
+
+def gnp_binomial(undirected, n, p, seed, P, k_leaf=K_LEAF, k_max=K_MAX, cap_hint=None):
+    """G(n,p) by binomial chunk counts and the G(n,m) sampler (Sec. 4.3)."""
+    L = lib()
+    cap = cap_hint if cap_hint is not None else 1 << 16
+    while True:
+        u = np.zeros(max(cap, 1), dtype=np.uint64)
+        v = np.zeros(max(cap, 1), dtype=np.uint64)
+        cnt = ctypes.c_uint64()
+        rc = L.or_gnp_binomial(1 if undirected else 0, n, p, seed, P, k_leaf, k_max, _p64(u),
+                               _p64(v), cap, ctypes.byref(cnt))
+        if rc == 3:
+            cap = cnt.value
+            continue
+        _check(rc, "gnp_binomial")
         return u[:cnt.value], v[:cnt.value]
 
 

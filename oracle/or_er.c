@@ -24,6 +24,7 @@
 #define TAG_TILE 3u
 #define TAG_LEAF 4u
 #define TAG_GNP 5u
+#define TAG_GNP_COUNT 6u
 
 /* ---------------- growable edge buffer ---------------- */
 
@@ -177,9 +178,8 @@ int or_floyd_leaf(uint64_t L, uint64_t k, uint64_t seed, uint64_t node, uint64_t
  * smallest d with E <= k_leaf 2^d, where E = m (U_nom / N) is the expected
  * sample count of a chunk of the nominal (largest possible) universe U_nom.
  * It depends only on (n, m, P), not on sampled counts. */
-static int tile_depth(uint64_t m, u128 Unom, u128 Ntot, uint32_t k_leaf, int *d_out)
+static int tile_depth_e(double E, u128 Unom, uint32_t k_leaf, int *d_out)
 {
-    double E = (double)m * (or_dbl128(Unom) / or_dbl128(Ntot));
     int d = 0;
     for (;;) {
         if (E <= (double)k_leaf * (double)((uint64_t)1 << d))
@@ -192,6 +192,12 @@ static int tile_depth(uint64_t m, u128 Unom, u128 Ntot, uint32_t k_leaf, int *d_
     }
     *d_out = d;
     return 0;
+}
+
+static int tile_depth(uint64_t m, u128 Unom, u128 Ntot, uint32_t k_leaf, int *d_out)
+{
+    double E = (double)m * (or_dbl128(Unom) / or_dbl128(Ntot));
+    return tile_depth_e(E, Unom, k_leaf, d_out);
 }
 
 typedef struct {
@@ -737,6 +743,103 @@ int or_gnp(int undirected, uint64_t n, double p, uint64_t seed, uint32_t P, uint
                 free(offs);
             }
     }
+    if (!rc)
+        rc = finish_sorted(&b, u, v, cap, count);
+    free(b.e);
+    return rc;
+}
+
+/* ---------------- G(n,p) by binomial chunk counts, Sec. 4.3 ---------------- */
+
+/* Sec. 4.3: the sample count of every chunk is a binomial variate drawn from
+ * a stream keyed by the chunk id, so that every PE needing the count draws
+ * the same value; the chunk is then sampled exactly like a G(n,m) chunk
+ * (tile tree + Floyd), with one tile depth per instance from the expected
+ * count p U_nom of the nominal chunk.  Chunks: directed c = 0..P-1 (stream id
+ * c); undirected (i, j), j <= i, in the order k = i(i+1)/2 + j (stream id
+ * i P + j).  Chunk universes are limited to 2^53 pairs. */
+static int gnp_binomial_check(int undirected, uint64_t n, double p, uint32_t P)
+{
+    if (!(p >= 0.0 && p <= 1.0))
+        return 1;
+    int rc = undirected ? check_undirected(n, 0, P) : check_directed(n, 0, P);
+    if (rc)
+        return rc;
+    u128 rmax = ((u128)n + P - 1) / P;
+    u128 Unom = undirected ? rmax * rmax : rmax * (n - 1);
+    return Unom > (u128)OR_BINOM_N_MAX ? 2 : 0;
+}
+
+int or_gnp_binomial_counts(int undirected, uint64_t n, double p, uint64_t seed, uint32_t P,
+                           uint64_t *cnt)
+{
+    int rc = gnp_binomial_check(undirected, n, p, P);
+    if (rc)
+        return rc;
+    uint64_t k = 0;
+    for (uint32_t i = 0; !rc && i < P; i++) {
+        if (!undirected) {
+            uint64_t Uc = (row_bound(n, P, (uint64_t)i + 1) - row_bound(n, P, i)) * (n - 1);
+            or_stream s = or_stream_make(seed, i, TAG_GNP_COUNT);
+            rc = or_binom_big(Uc, p, &s, &cnt[i]);
+            continue;
+        }
+        for (uint32_t j = 0; !rc && j <= i; j++, k++) {
+            or_stream s = or_stream_make(seed, (uint64_t)i * P + j, TAG_GNP_COUNT);
+            rc = or_binom_big(und_chunk_universe(n, P, i, j), p, &s, &cnt[k]);
+        }
+    }
+    return rc;
+}
+
+int or_gnp_binomial(int undirected, uint64_t n, double p, uint64_t seed, uint32_t P,
+                    uint32_t k_leaf, uint32_t k_max, uint64_t *u, uint64_t *v, uint64_t cap,
+                    uint64_t *count)
+{
+    if (k_leaf < 2 || k_max < k_leaf)
+        return 1;
+    int rc = gnp_binomial_check(undirected, n, p, P);
+    if (rc)
+        return rc;
+    uint64_t C = undirected ? (uint64_t)P * (P + 1) / 2 : P;
+    uint64_t *cnt = (uint64_t *)malloc(C * sizeof(uint64_t));
+    if (!cnt)
+        return 1;
+    rc = or_gnp_binomial_counts(undirected, n, p, seed, P, cnt);
+    u128 rmax = ((u128)n + P - 1) / P;
+    u128 Unom = undirected ? rmax * rmax : rmax * (n - 1);
+    int d = 0;
+    if (!rc)
+        rc = tile_depth_e(p * or_dbl128(Unom), Unom, k_leaf, &d);
+    edge_buf b = {0, 0, 0, 0};
+    uint64_t k = 0;
+    for (uint32_t i = 0; !rc && i < P; i++)
+        for (uint32_t j = 0; !rc && j <= (undirected ? i : 0); j++, k++) {
+            uint64_t kc = cnt[k];
+            uint64_t cid = undirected ? (uint64_t)i * P + j : i;
+            uint64_t r0 = row_bound(n, P, i);
+            uint64_t Uc = undirected ? und_chunk_universe(n, P, i, j)
+                                     : (row_bound(n, P, (uint64_t)i + 1) - r0) * (n - 1);
+            uint64_t *offs = (uint64_t *)malloc((kc ? kc : 1) * sizeof(uint64_t));
+            if (!offs) {
+                rc = 1;
+                break;
+            }
+            rc = chunk_offsets(seed, cid, Uc, d, k_max, kc, offs);
+            for (uint64_t t = 0; !rc && t < kc; t++) {
+                if (undirected) {
+                    uint64_t uu, vv;
+                    und_map(n, P, i, j, offs[t], &uu, &vv);
+                    eb_push(&b, uu, vv);
+                    eb_push(&b, vv, uu);
+                } else {
+                    uint64_t uu = r0 + offs[t] / (n - 1), w = offs[t] % (n - 1);
+                    eb_push(&b, uu, w + (w >= uu ? 1 : 0));
+                }
+            }
+            free(offs);
+        }
+    free(cnt);
     if (!rc)
         rc = finish_sorted(&b, u, v, cap, count);
     free(b.e);

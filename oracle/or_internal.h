@@ -26,9 +26,11 @@ double or_dbl128(u128 x);          /* round-to-nearest-even conversion */
 /* variates: all consume the stream in order */
 int or_hyper_s(u128 N, u128 K, uint64_t t, or_stream *s, uint64_t *x);
 int or_binom_s(uint64_t n, double p, or_stream *s, uint64_t *x);
+int or_binom_big(uint64_t n, double p, or_stream *s, uint64_t *x);
 
 /* limits of the procedure */
 #define OR_M_MAX ((uint64_t)1 << 44)  /* largest m (and binomial n) accepted */
+#define OR_BINOM_N_MAX ((uint64_t)1 << 53) /* largest binomial n for G(n,p) chunk counts */
 #define OR_D_MAX 24                     /* largest tile-tree depth */
 #define OR_LEVEL_MAX 31                 /* tile heap index must stay below 2^32 */
 #define OR_REJECT_CAP 1000000           /* rejection/restart loop cap */

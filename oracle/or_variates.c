@@ -81,7 +81,7 @@ static int binom_rou(uint64_t n, double p, or_stream *s, uint64_t *out)
     return 6;
 }
 
-int or_binom_s(uint64_t n, double p, or_stream *s, uint64_t *x)
+static int binom_upto(uint64_t n, double p, or_stream *s, uint64_t *x, uint64_t nmax)
 {
     if (n == 0 || p <= 0.0) {
         *x = 0;
@@ -91,7 +91,7 @@ int or_binom_s(uint64_t n, double p, or_stream *s, uint64_t *x)
         *x = n;
         return 0;
     }
-    if (n > OR_M_MAX)
+    if (n > nmax)
         return 2;
     int flip = p > 0.5;
     double pp = flip ? 1.0 - p : p;
@@ -101,6 +101,18 @@ int or_binom_s(uint64_t n, double p, or_stream *s, uint64_t *x)
         return rc;
     *x = flip ? n - r : r;
     return 0;
+}
+
+int or_binom_s(uint64_t n, double p, or_stream *s, uint64_t *x)
+{
+    return binom_upto(n, p, s, x, OR_M_MAX);
+}
+
+/* The same variate for n up to 2^53 (every count and n - x stays exact in a
+ * double): the chunk counts of G(n,p), Sec. 4.3. */
+int or_binom_big(uint64_t n, double p, or_stream *s, uint64_t *x)
+{
+    return binom_upto(n, p, s, x, OR_BINOM_N_MAX);
 }
 
 /* ---------------- hypergeometric ---------------- */

@@ -64,6 +64,14 @@ int or_gnm_undirected(uint64_t n, uint64_t m, uint64_t seed, uint32_t P,
 int or_gnp(int undirected, uint64_t n, double p, uint64_t seed, uint32_t P,
            uint32_t k_leaf, uint64_t *u, uint64_t *v, uint64_t cap, uint64_t *count);
 
+/* ---- G(n,p) by binomial chunk counts + the G(n,m) sampler, Sec. 4.3 ---- */
+/* cnt: P (directed) or P(P+1)/2 (undirected, order k = i(i+1)/2 + j) counts */
+int or_gnp_binomial_counts(int undirected, uint64_t n, double p, uint64_t seed, uint32_t P,
+                           uint64_t *cnt);
+int or_gnp_binomial(int undirected, uint64_t n, double p, uint64_t seed, uint32_t P,
+                    uint32_t k_leaf, uint32_t k_max, uint64_t *u, uint64_t *v, uint64_t cap,
+                    uint64_t *count);
+
 /* ---- order-independent edge-list digest ---- */
 uint64_t or_edge_checksum(const uint64_t *u, const uint64_t *v, uint64_t count);
 /* out-degree histogram over vertices [row_lo, row_hi): hist[d] for d<64, hist[64] for d>=64.

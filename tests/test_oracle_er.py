@@ -251,6 +251,95 @@ def test_gnp_extremes(orc):
     check_simple(u, v, 7, directed=False)
 
 
+# ------------------------------------------- G(n,p) by binomial chunk counts
+
+def _graph_law(orc_fn, undirected, n, p, S):
+    pairs = [(a, b) for a in range(n) for b in range(n) if a != b and (not undirected or a > b)]
+    counts = Counter()
+    for seed in range(S):
+        u, v = orc_fn(seed)
+        counts[tuple((a, b) for a, b in zip(u.tolist(), v.tolist()) if (not undirected or a > b))] += 1
+    Np = len(pairs)
+    by_size = Counter()
+    for g, c in counts.items():
+        by_size[len(g)] += c
+    obs = np.array([by_size.get(j, 0) for j in range(Np + 1)], dtype=float)
+    exp_ = np.array([math.comb(Np, j) * p ** j * (1 - p) ** (Np - j) for j in range(Np + 1)]) * S
+    mask = exp_ >= 5
+    chi2 = float(((obs[mask] - exp_[mask]) ** 2 / exp_[mask]).sum())
+    assert stats.chi2.sf(chi2, mask.sum() - 1) > P_MIN
+    # within each edge count every graph is equally likely
+    for j in range(Np + 1):
+        graphs = {g: c for g, c in counts.items() if len(g) == j}
+        cells = math.comb(Np, j)
+        if cells > 1 and by_size.get(j, 0) >= 20 * cells:
+            assert chi2_uniform(Counter(graphs), cells) > P_MIN, j
+
+
+@pytest.mark.parametrize("undirected,n,P", [(False, 3, 1), (False, 3, 3), (True, 4, 2), (True, 4, 4)])
+def test_gnp_binomial_exact_graph_law(orc, undirected, n, P):
+    """Sec. 4.3 with binomial chunk counts: P(graph) = p^|E| (1-p)^(N-|E|),
+    with leaves of two samples so the tile tree and Floyd are both used."""
+    p = 0.35
+    _graph_law(lambda seed: orc.gnp_binomial(undirected, n, p, seed, P, 2, 2), undirected, n, p,
+               20000)
+
+
+@pytest.mark.parametrize("mean", [4.0, 100.0])
+def test_gnp_binomial_chunk_count_law_at_2e52_pairs(orc, mean):
+    """One chunk of n(n-1) ~ 2^52 pairs: its count is Binomial(U, p), drawn by
+    inversion (mean 4) or ratio of uniforms (mean 100) at a size beyond the
+    G(n,m) limit."""
+    n = 1 << 26
+    U = n * (n - 1)
+    p = mean / U
+    S = 3000
+    x = np.array([int(orc.gnp_binomial_counts(False, n, p, seed, 1)[0]) for seed in range(S)])
+    kmax = int(x.max())
+    obs = np.bincount(x, minlength=kmax + 1).astype(float)
+    pm = stats.binom.pmf(np.arange(kmax + 1), U, p)
+    pm[-1] += stats.binom.sf(kmax, U, p)
+    e = pm * S
+    mask = e >= 5
+    o2, e2 = obs[mask], e[mask]
+    rest_o, rest_e = obs[~mask].sum(), e[~mask].sum()
+    chi2 = float(((o2 - e2) ** 2 / e2).sum()) + ((rest_o - rest_e) ** 2 / rest_e if rest_e > 0 else 0)
+    assert stats.chi2.sf(chi2, mask.sum()) > P_MIN
+
+
+@pytest.mark.parametrize("undirected,n,p,P", [(False, 3000, 2e-3, 16), (True, 1 << 14, 16 / ((1 << 14) - 1), 32)])
+def test_gnp_binomial_edge_count_and_degrees(orc, undirected, n, p, P):
+    u, v = orc.gnp_binomial(undirected, n, p, 11, P)
+    check_simple(u, v, n, directed=not undirected)
+    Npairs = n * (n - 1) // (2 if undirected else 1)
+    m = len(u) // (2 if undirected else 1)
+    assert abs((m - Npairs * p) / math.sqrt(Npairs * p * (1 - p))) < 5
+    cnt = orc.gnp_binomial_counts(undirected, n, p, 11, P)
+    assert int(cnt.sum()) == m      # the chunks hold exactly their binomial counts
+    deg = np.bincount(u.astype(np.int64), minlength=n)
+    kmax = int(deg.max())
+    obs = np.bincount(deg, minlength=kmax + 1).astype(float)
+    pm = stats.binom.pmf(np.arange(kmax + 1), n - 1, p)
+    pm[-1] += stats.binom.sf(kmax, n - 1, p)
+    e = pm * n
+    mask = e >= 5
+    o2, e2 = obs[mask], e[mask]
+    e2 = e2 * o2.sum() / e2.sum()
+    assert stats.chi2.sf(float(((o2 - e2) ** 2 / e2).sum()), mask.sum() - 1) > 1e-4
+
+
+def test_gnp_binomial_extremes_and_limits(orc):
+    u, v = orc.gnp_binomial(False, 50, 0.0, 1, 4)
+    assert len(u) == 0
+    u, v = orc.gnp_binomial(False, 7, 1.0, 1, 3)
+    assert len(u) == 42
+    u, v = orc.gnp_binomial(True, 9, 1.0, 1, 3)
+    assert len(u) == 72
+    check_simple(u, v, 9, directed=False)
+    with pytest.raises(RuntimeError):
+        orc.gnp_binomial_counts(False, 1 << 40, 1e-9, 1, 16)   # chunks of 2^66 pairs
+
+
 # ---------------------------------------------------------------- digests
 
 def test_checksum_is_order_independent_and_sensitive(orc):
