@@ -130,6 +130,24 @@ kg_status kg_gnp_ex(int undirected, uint64_t n, double p, uint64_t seed, uint32_
                     uint64_t* d_count, void* stream);
 
 /*
+ * G(n,p) by binomial chunk counts, Sec. 4.3: the sample count of every chunk
+ * is a binomial variate Binomial(U_c, p) drawn from the stream of (seed, chunk
+ * id), and the chunk is then sampled exactly like a G(n,m) chunk (tile tree +
+ * Floyd's algorithm).  Same law as kg_gnp_ex, a different graph for the same
+ * seed.  Chunks as for G(n,m); the chunk universes must not exceed 2^53
+ * pairs (KG_ERR_RANGE), so that the binomial's counts stay exact doubles.
+ * *d_count (device, uint64) receives the number of entries (both directions
+ * when undirected); beyond cap_edges the device error word becomes
+ * KG_ERR_CAPACITY.  kg_gnp_binomial_count writes only *d_count (the chunk
+ * binomials and their sum), the exact size of the same call's output.
+ */
+kg_status kg_gnp_binomial(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
+                          int id_bytes, void* d_out, uint64_t cap_edges, uint64_t* d_count,
+                          void* stream);
+kg_status kg_gnp_binomial_count(int undirected, uint64_t n, double p, uint64_t seed,
+                                uint32_t chunks, uint64_t* d_count, void* stream);
+
+/*
  * kg_gnm_directed_noalloc -- directed G(n,m) that allocates no memory.
  * The paper has no counterpart to this entry point; it exists for callers
  * that must not let a library allocate device memory: a framework whose

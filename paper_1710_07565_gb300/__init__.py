@@ -60,6 +60,8 @@ def lib() -> ctypes.CDLL:
                 "kg_gnp_directed": [u64, dbl, u64, u32, i32, vp, u64, vp, vp],
                 "kg_gnp_undirected": [u64, dbl, u64, u32, i32, vp, u64, vp, vp],
                 "kg_gnp_ex": [i32, u64, dbl, u64, u32, u32, i32, vp, u64, vp, vp],
+                "kg_gnp_binomial": [i32, u64, dbl, u64, u32, i32, vp, u64, vp, vp],
+                "kg_gnp_binomial_count": [i32, u64, dbl, u64, u32, vp, vp],
                 "kg_edge_digest": [vp, u64, i32, vp, vp],
                 "kg_last_error": [vp],
                 "kg_gnm_directed_noalloc": [u64, u64, u64, u32, i32, vp, u64, vp, vp],
@@ -174,6 +176,15 @@ def kg_gnp_undirected(n, p, seed, chunks, id_bytes, d_out, cap_edges, d_count, s
 def kg_gnp_ex(undirected, n, p, seed, chunks, k_leaf, id_bytes, d_out, cap_edges, d_count, stream):
     return _call("kg_gnp_ex", int(undirected), n, p, seed, chunks, k_leaf, id_bytes, d_out,
                  cap_edges, d_count, stream)
+
+
+def kg_gnp_binomial(undirected, n, p, seed, chunks, id_bytes, d_out, cap_edges, d_count, stream):
+    return _call("kg_gnp_binomial", int(undirected), n, p, seed, chunks, id_bytes, d_out,
+                 cap_edges, d_count, stream)
+
+
+def kg_gnp_binomial_count(undirected, n, p, seed, chunks, d_count, stream):
+    return _call("kg_gnp_binomial_count", int(undirected), n, p, seed, chunks, d_count, stream)
 
 
 def kg_gnm_directed_noalloc(n, m, seed, chunks, id_bytes, d_out, cap_edges, d_status, stream):
@@ -378,3 +389,16 @@ def gnp(undirected, n, p, seed=1, chunks=1, id_bytes=4, k_leaf=K_LEAF_DEFAULT, c
     kg_gnp_ex(undirected, n, p, seed, chunks, k_leaf, id_bytes, out.data_ptr(), cap, cnt.data_ptr(),
               _stream_ptr(stream))
     return out, cnt
+
+
+def gnp_binomial(undirected, n, p, seed=1, chunks=1, id_bytes=4, stream=None, device="cuda"):
+    """G(n,p) by binomial chunk counts (Sec. 4.3): sized exactly first, then
+    generated; returns the edges tensor."""
+    import torch
+    s = _stream_ptr(stream)
+    cnt = torch.zeros(1, dtype=torch.int64, device=device)
+    kg_gnp_binomial_count(undirected, n, p, seed, chunks, cnt.data_ptr(), s)
+    k = int(cnt.item())
+    out = _empty_edges(max(k, 1), id_bytes, device)
+    kg_gnp_binomial(undirected, n, p, seed, chunks, id_bytes, out.data_ptr(), k, cnt.data_ptr(), s)
+    return out[:k]

@@ -219,6 +219,81 @@ static int gnp_dispatch_slots(const Geom& g, uint64_t C, bool und, uint64_t n, c
 
 using namespace kg;
 
+// ---------------------------------------------------------------- G(n,p), binomial counts
+// Validation shared by kg_gnp_binomial and kg_gnp_binomial_count: chunk
+// universes up to 2^53 (the binomial's exact range), the tile depth from the
+// expected count p U_nom of the nominal chunk.
+static int gnpb_prepare(int undirected, uint64_t n, double p, uint32_t chunks, int id_bytes,
+                        uint64_t& C, int& d) {
+  if (!(p >= 0.0 && p <= 1.0)) return ST_ARG;
+  if (n == 0 || chunks == 0 || uint64_t(chunks) > n) return ST_ARG;
+  if (id_bytes != 4 && id_bytes != 8) return ST_ARG;
+  if (id_bytes == 4 && n > (uint64_t(1) << 32)) return ST_RANGE;
+  const u128 rmax = (u128(n) + chunks - 1) / chunks;
+  u128 Unom;
+  if (undirected) {
+    if (chunks > 65536u || n > (uint64_t(1) << 31)) return ST_RANGE;
+    Unom = rmax * rmax;
+    C = uint64_t(chunks) * (chunks + 1) / 2;
+  } else {
+    if (chunks > (1u << 24)) return ST_RANGE;
+    Unom = rmax * (n - 1);
+    C = chunks;
+  }
+  if (Unom > u128(BINOM_N_MAX)) return ST_RANGE;
+  return tile_depth_e(p * dbl(Unom), Unom, K_LEAF, d);
+}
+
+template <class Geom>
+static int gnpb_counts(const Geom& g, uint64_t C, double p, uint64_t seed, uint64_t* cnt,
+                       cudaStream_t s, int* err) {
+  ProfScope ps(PROF_CHUNK_TREE, s);
+  gnp_chunk_counts<Geom><<<grid_for(C, 128, 152 * 16), 128, 0, s>>>(g, C, p, seed, cnt, err);
+  return launch_ok();
+}
+
+template <class Id>
+static int gnpb_impl(int undirected, uint64_t n, double p, uint64_t seed, uint32_t P, uint64_t C,
+                     int d, void* d_out, uint64_t cap, uint64_t* d_count, cudaStream_t s,
+                     int* err) {
+  Workspace ws(s);
+  uint64_t* cnt = ws.alloc<uint64_t>(C);
+  uint64_t* off = ws.alloc<uint64_t>(C + 1);
+  uint64_t* npairs = ws.alloc<uint64_t>(1);
+  if (!ws.ok()) return ST_CUDA;
+  const uint64_t mult = undirected ? 2 : 1;
+  int st;
+  if (!undirected) {
+    DirGeom g;
+    g.n = n;
+    g.P = P;
+    g.div = make_div(n - 1);
+    g.rb = RowBounds::make(n, P);
+    if ((st = gnpb_counts(g, C, p, seed, cnt, s, err))) return st;
+    if ((st = scan_exclusive_u64(cnt, off, C, ws, s))) return st;
+    {
+      ProfScope ps(PROF_OTHER, s);
+      gnp_total<<<1, 1, 0, s>>>(off + C, d_count, npairs, mult, cap, err);
+      if (launch_ok()) return ST_CUDA;
+    }
+    return run_chunks(g, 0, C, cnt, d, K_MAX, seed, int(sizeof(Id)), d_out, cap, ws, s, err);
+  }
+  UndGeom g{n, P, RowBounds::make(n, P)};
+  if ((st = gnpb_counts(g, C, p, seed, cnt, s, err))) return st;
+  if ((st = scan_exclusive_u64(cnt, off, C, ws, s))) return st;
+  {
+    ProfScope ps(PROF_OTHER, s);
+    gnp_total<<<1, 1, 0, s>>>(off + C, d_count, npairs, mult, cap, err);
+    if (launch_ok()) return ST_CUDA;
+  }
+  const uint64_t pcap = cap / 2;
+  Id* pairs = ws.alloc<Id>(2 * (pcap ? pcap : 1));
+  if (!ws.ok()) return ST_CUDA;
+  if ((st = run_chunks(g, 0, C, cnt, d, K_MAX, seed, int(sizeof(Id)), pairs, pcap, ws, s, err)))
+    return st;
+  return assemble<Id>(pairs, npairs, 0, n, static_cast<Id*>(d_out), cap, ws, s, err);
+}
+
 extern "C" {
 
 kg_status kg_gnm_undirected_ex(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
@@ -336,6 +411,61 @@ kg_status kg_gnp_count(int undirected, uint64_t n, double p, uint64_t seed, uint
     st = gnp_count_impl(g, C, false, pl, seed, d_count, s, err);
   }
   return kg_status(st);
+}
+
+kg_status kg_gnp_binomial(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
+                          int id_bytes, void* d_out, uint64_t cap_edges, uint64_t* d_count,
+                          void* stream) {
+  if (!d_count) return KG_ERR_ARG;
+  uint64_t C = 0;
+  int d = 0;
+  int st = gnpb_prepare(undirected, n, p, chunks, id_bytes, C, d);
+  if (st) return kg_status(st);
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s) != cudaSuccess) return KG_ERR_CUDA;
+  if (p == 0.0 || n < 2) return KG_OK;
+  if (!d_out && cap_edges > 0) return KG_ERR_ARG;
+  int* err = device_error_word();
+  if (!err) return KG_ERR_CUDA;
+  st = id_bytes == 4 ? gnpb_impl<uint32_t>(undirected, n, p, seed, chunks, C, d, d_out, cap_edges,
+                                           d_count, s, err)
+                     : gnpb_impl<uint64_t>(undirected, n, p, seed, chunks, C, d, d_out, cap_edges,
+                                           d_count, s, err);
+  return kg_status(st);
+}
+
+kg_status kg_gnp_binomial_count(int undirected, uint64_t n, double p, uint64_t seed,
+                                uint32_t chunks, uint64_t* d_count, void* stream) {
+  if (!d_count) return KG_ERR_ARG;
+  uint64_t C = 0;
+  int d = 0;
+  int st = gnpb_prepare(undirected, n, p, chunks, 8, C, d);
+  if (st) return kg_status(st);
+  cudaStream_t s = as_stream(stream);
+  if (cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s) != cudaSuccess) return KG_ERR_CUDA;
+  if (p == 0.0 || n < 2) return KG_OK;
+  int* err = device_error_word();
+  if (!err) return KG_ERR_CUDA;
+  Workspace ws(s);
+  uint64_t* cnt = ws.alloc<uint64_t>(C);
+  uint64_t* off = ws.alloc<uint64_t>(C + 1);
+  if (!ws.ok()) return KG_ERR_CUDA;
+  if (undirected) {
+    UndGeom g{n, chunks, RowBounds::make(n, chunks)};
+    st = gnpb_counts(g, C, p, seed, cnt, s, err);
+  } else {
+    DirGeom g;
+    g.n = n;
+    g.P = chunks;
+    g.div = make_div(n - 1);
+    g.rb = RowBounds::make(n, chunks);
+    st = gnpb_counts(g, C, p, seed, cnt, s, err);
+  }
+  if (st) return kg_status(st);
+  if ((st = scan_exclusive_u64(cnt, off, C, ws, s))) return kg_status(st);
+  ProfScope ps(PROF_OTHER, s);
+  gnp_total<<<1, 1, 0, s>>>(off + C, d_count, nullptr, undirected ? 2 : 1, ~uint64_t(0), err);
+  return kg_status(launch_ok());
 }
 
 kg_status kg_gnp_directed(uint64_t n, double p, uint64_t seed, uint32_t chunks, int id_bytes,

@@ -37,10 +37,12 @@ enum : uint32_t {
   TAG_TILE = 3u,        // tile tree inside a chunk, node = chunk<<32 | heap
   TAG_LEAF = 4u,        // Floyd draws of a leaf, node = chunk<<32 | heap
   TAG_GNP = 5u,         // geometric skips of a G(n,p) tile, node = chunk<<32 | tile
+  TAG_GNP_COUNT = 6u,   // binomial sample count of a G(n,p) chunk, node = chunk id
 };
 
 // Limits of the procedure.
 constexpr uint64_t M_MAX = uint64_t(1) << 44;  // largest m / binomial n
+constexpr uint64_t BINOM_N_MAX = uint64_t(1) << 53;  // largest n of a G(n,p) chunk count
 constexpr int D_MAX = 24;                      // largest tile-tree depth
 constexpr int LEVEL_MAX = 31;                  // heap index < 2^32
 constexpr int REJECT_CAP = 1000000;            // rejection loop cap
@@ -302,8 +304,11 @@ __host__ __device__ __forceinline__ int binom_rou(uint64_t n, double p, Stream& 
   return ST_INTERNAL;
 }
 
-// Binomial(n, p): inversion for n min(p,1-p) < 10, else ratio of uniforms.
-__host__ __device__ __forceinline__ int binomial(uint64_t n, double p, Stream& s, uint64_t& out) {
+// Binomial(n, p): inversion for n min(p,1-p) < 10, else ratio of uniforms;
+// n up to nmax (M_MAX for the hypergeometric's binomial regime, BINOM_N_MAX
+// for the chunk counts of G(n,p): every count and n - x stay exact doubles).
+__host__ __device__ __forceinline__ int binomial(uint64_t n, double p, Stream& s, uint64_t& out,
+                                                 uint64_t nmax = M_MAX) {
   if (n == 0 || p <= 0.0) {
     out = 0;
     return ST_OK;
@@ -312,7 +317,7 @@ __host__ __device__ __forceinline__ int binomial(uint64_t n, double p, Stream& s
     out = n;
     return ST_OK;
   }
-  if (n > M_MAX) return ST_RANGE;
+  if (n > nmax) return ST_RANGE;
   const bool flip = p > 0.5;
   const double pp = flip ? 1.0 - p : p;
   uint64_t r = 0;

@@ -110,4 +110,24 @@ __global__ void __launch_bounds__(128)
   }
 }
 
+// Sec. 4.3 with binomial chunk counts: the sample count of chunk c is
+// Binomial(U_c, p) from the stream (seed, chunk id, TAG_GNP_COUNT); the chunk
+// is then sampled like a G(n,m) chunk.  One thread per chunk.
+template <class Geom>
+__global__ void __launch_bounds__(128)
+    gnp_chunk_counts(Geom g, uint64_t C, double p, uint64_t seed, uint64_t* __restrict__ cnt,
+                     int* err) {
+  for (uint64_t c = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < C;
+       c += uint64_t(gridDim.x) * blockDim.x) {
+    Stream s(seed, g.chunk_id(c), TAG_GNP_COUNT);
+    uint64_t x = 0;
+    const int e = binomial(g.universe(c), p, s, x, BINOM_N_MAX);
+    if (e) {
+      set_error(err, e);
+      x = 0;
+    }
+    cnt[c] = x;
+  }
+}
+
 }  // namespace kg

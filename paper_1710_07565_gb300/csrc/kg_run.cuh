@@ -7,10 +7,10 @@
 
 namespace kg {
 
-// Tile-tree depth, one per instance: smallest d with E <= k_leaf 2^d, where
-// E = m (U_nom / N) is the expected count of a chunk of nominal universe U_nom.
-inline int tile_depth(uint64_t m, u128 Unom, u128 Ntot, uint32_t k_leaf, int& d_out) {
-  const double E = double(m) * (dbl(Unom) / dbl(Ntot));
+// Tile-tree depth, one per instance: smallest d with E <= k_leaf 2^d, where E
+// is the expected count of a chunk of nominal universe U_nom (d stops once
+// 2^(d+1) > U_nom).
+inline int tile_depth_e(double E, u128 Unom, uint32_t k_leaf, int& d_out) {
   int d = 0;
   for (;;) {
     if (E <= double(k_leaf) * double(uint64_t(1) << d)) break;
@@ -20,6 +20,11 @@ inline int tile_depth(uint64_t m, u128 Unom, u128 Ntot, uint32_t k_leaf, int& d_
   }
   d_out = d;
   return ST_OK;
+}
+
+// G(n,m): E = m (U_nom / N).
+inline int tile_depth(uint64_t m, u128 Unom, u128 Ntot, uint32_t k_leaf, int& d_out) {
+  return tile_depth_e(double(m) * (dbl(Unom) / dbl(Ntot)), Unom, k_leaf, d_out);
 }
 
 inline unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {

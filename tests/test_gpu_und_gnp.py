@@ -108,3 +108,50 @@ def test_gnp_zero_and_capacity(kg):
     assert L.kg_gnp_ex(1, 10, 0.5, 1, 11, 1024, 4, out.data_ptr(), 8, cnt.data_ptr(), s) == kg.KG_ERR_ARG
     assert L.kg_gnm_undirected(10, 46, 1, 2, 4, out.data_ptr(), 100, s) == kg.KG_ERR_ARG
     assert L.kg_gnm_undirected(10, 5, 1, 2, 4, out.data_ptr(), 9, s) == kg.KG_ERR_CAPACITY
+
+
+# ---------------------------------------------------------------- G(n,p), binomial chunk counts
+
+GNPB_CASES = [
+    # undirected, n, p, seed, P, id_bytes
+    (False, 1000, 0.01, 3, 7, 4),
+    (False, 3000, 0.5, 4, 16, 4),              # dense: Floyd replacements in most leaves
+    (False, 64, 1.0, 5, 4, 8),                 # every pair
+    (False, 1 << 20, 4 / (1 << 20), 6, 64, 8),  # binomial at 2^34-pair chunks
+    (True, 5000, 0.01, 7, 31, 4),
+    (True, 300, 0.5, 8, 300, 4),               # one vertex per block
+    (True, 1 << 20, 16 / ((1 << 20) - 1), 1, 32, 4),  # the n = 2^20, degree-16 instance
+]
+
+
+@pytest.mark.parametrize("und,n,p,seed,P,id_bytes", GNPB_CASES)
+def test_gnp_binomial_bit_exact(kg, orc, und, n, p, seed, P, id_bytes):
+    import torch
+    t = kg.gnp_binomial(und, n, p, seed, P, id_bytes)
+    kg.check_device_error()
+    gu, gv = edges_np(t, id_bytes)
+    mean = n * (n - 1) * p / (1 if not und else 2)
+    ou, ov = orc.gnp_binomial(und, n, p, seed, P, cap_hint=int(2 * mean + 1024) * 2)
+    assert_same_edges(gu, gv, ou, ov, f"gnp_binomial und={und} n={n} p={p} P={P}")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    kg.kg_gnp_binomial_count(und, n, p, seed, P, cnt.data_ptr(), kg._stream_ptr(None))
+    assert int(cnt.item()) == len(ou)
+
+
+def test_gnp_binomial_zero_capacity_and_range(kg):
+    import torch
+    s = kg._stream_ptr(None)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    out = torch.zeros((16, 2), dtype=torch.int32, device="cuda")
+    kg.kg_gnp_binomial(False, 100, 0.0, 1, 4, 4, out.data_ptr(), 16, cnt.data_ptr(), s)
+    kg.check_device_error()
+    assert int(cnt.item()) == 0 and int(out.abs().sum()) == 0
+    L = kg.lib()
+    # 100 x 99 pairs at p = 1/2 do not fit 16 slots: the count is exact, the error recorded
+    assert L.kg_gnp_binomial(0, 100, 0.5, 1, 4, 4, out.data_ptr(), 16, cnt.data_ptr(), s) == 0
+    torch.cuda.synchronize()
+    assert L.kg_last_error(s) == kg.KG_ERR_CAPACITY
+    assert int(cnt.item()) > 16
+    # chunks of 2^66 pairs are beyond the binomial's exact range
+    assert L.kg_gnp_binomial(0, 1 << 40, 1e-9, 1, 16, 8, out.data_ptr(), 16, cnt.data_ptr(), s) \
+        == kg.KG_ERR_RANGE
