@@ -200,6 +200,16 @@ def other_workloads(kg, serve_requests=1000):
         "ms": ms, "entries": k, "entries_per_s": k / ms * 1e3, "write_GBps": k * 8 / ms / 1e6,
         "bound": "fp64 (one log per kept pair)", "fp64_ops_per_s_est": (k // 2) * 45 / ms * 1e3}
     del out, cnt
+    # the same instance by binomial chunk counts + the G(n,m) sampler (Sec. 4.3)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    kg.kg_gnp_binomial_count(True, n, p, 1, 32, cnt.data_ptr(), s)
+    kb = int(cnt.item())
+    out = torch.empty((kb, 2), dtype=torch.int32, device="cuda")
+    ms = _timed(lambda: kg.kg_gnp_binomial(True, n, p, 1, 32, 4, out.data_ptr(), kb, cnt.data_ptr(),
+                                           s), 5)
+    res["gnp_binomial_undirected_n2e20_avgdeg16_P32"] = {
+        "ms": ms, "entries": kb, "entries_per_s": kb / ms * 1e3, "write_GBps": kb * 8 / ms / 1e6}
+    del out, cnt
     kg.check_device_error()
     # batched: 4096 instances, one launch sequence (CUDA graph) vs 4096 separate calls
     insts = workloads.batched_instances(4096)

@@ -239,7 +239,8 @@ kg_status kg_gnp_count(int undirected, uint64_t n, double p, uint64_t seed, uint
  * running.  Not thread-safe: one host thread drives a server.
  */
 typedef struct kg_request {
-  int32_t model;      /* 0: G(n,m), 1: G(n,p) */
+  int32_t model;      /* 0: G(n,m), 1: G(n,p) by skips (kg_gnp_ex),
+                         2: G(n,p) by binomial chunk counts (kg_gnp_binomial) */
   int32_t undirected; /* 0 or 1 */
   uint64_t n, m;      /* m for G(n,m) */
   double p;           /* p for G(n,p) */

@@ -272,6 +272,10 @@ def kg_gnp_count(undirected, n, p, seed, chunks, k_leaf, d_count, stream):
     return _call("kg_gnp_count", int(undirected), n, p, seed, chunks, k_leaf, d_count, stream)
 
 
+# request models: G(n,m); G(n,p) by geometric skips; G(n,p) by binomial chunk counts
+_MODELS = {"gnm": 0, "gnp": 1, "gnp_binomial": 2}
+
+
 class kg_request(ctypes.Structure):
     _fields_ = [("model", ctypes.c_int32), ("undirected", ctypes.c_int32), ("n", ctypes.c_uint64),
                 ("m", ctypes.c_uint64), ("p", ctypes.c_double), ("seed", ctypes.c_uint64),
@@ -291,7 +295,7 @@ def kg_server_create(budget_bytes, streams):
 
 
 def kg_server_submit(h, req: dict, id_bytes=4) -> int:
-    r = kg_request(1 if req["model"] == "gnp" else 0, 1 if req["undirected"] else 0, req["n"],
+    r = kg_request(_MODELS[req["model"]], 1 if req["undirected"] else 0, req["n"],
                    req.get("m", 0), req.get("p", 0.0), req["seed"], req["chunks"], id_bytes)
     out = ctypes.c_uint64()
     _call("kg_server_submit", h, ctypes.byref(r), ctypes.byref(out))

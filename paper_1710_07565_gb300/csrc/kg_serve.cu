@@ -3,7 +3,8 @@
 // Requests (G(n,m) or G(n,p), directed or undirected) are admitted in arrival
 // order when their exact output size fits in a fixed device budget; the size
 // of a G(n,m) request is m or 2m entries, that of a G(n,p) request is counted
-// first on the device (kg_gnp_count, same skip walks without storing them).
+// first on the device (kg_gnp_count: the same skip walks without storing
+// them; kg_gnp_binomial_count: the chunk binomials of Sec. 4.3).
 // Admitted requests run on a set of streams, so requests that arrive while
 // others are on the GPU overlap with them; a request's output is reduced on
 // the device to its order-independent digest, copied to host memory, and its
@@ -117,9 +118,12 @@ static kg_status launch(kg_server* S, Req& r) {
   if (q.model == 0) {
     st = q.undirected ? kg_gnm_undirected(q.n, q.m, q.seed, q.chunks, q.id_bytes, out, r.entries, s)
                       : kg_gnm_directed(q.n, q.m, q.seed, q.chunks, q.id_bytes, out, r.entries, s);
-  } else {
+  } else if (q.model == 1) {
     st = kg_gnp_ex(q.undirected, q.n, q.p, q.seed, q.chunks, 1024, q.id_bytes, out, r.entries,
                    S->d_slots + 2 * r.slot, s);
+  } else {
+    st = kg_gnp_binomial(q.undirected, q.n, q.p, q.seed, q.chunks, q.id_bytes, out, r.entries,
+                         S->d_slots + 2 * r.slot, s);
   }
   if (st != KG_OK) return st;
   st = kg_edge_digest(out, r.entries, q.id_bytes, S->d_slots + 2 * r.slot + 1, s);
@@ -195,7 +199,7 @@ kg_status kg_server_destroy(kg_server* S) {
 }
 
 kg_status kg_server_submit(kg_server* S, const kg_request* q, uint64_t* id_out) {
-  if (!S || !q || (q->model != 0 && q->model != 1) || (q->id_bytes != 4 && q->id_bytes != 8))
+  if (!S || !q || (q->model < 0 || q->model > 2) || (q->id_bytes != 4 && q->id_bytes != 8))
     return KG_ERR_ARG;
   if (S->free_slots.empty()) return KG_ERR_CAPACITY;
   Req r;
@@ -211,8 +215,10 @@ kg_status kg_server_submit(kg_server* S, const kg_request* q, uint64_t* id_out) 
   } else {
     // exact size first: the count pass, its result copied to pinned memory
     cudaStream_t s = S->pick_stream(r.stream);
-    kg_status st = kg_gnp_count(q->undirected, q->n, q->p, q->seed, q->chunks, 1024,
-                                S->d_slots + 2 * r.slot, s);
+    kg_status st = q->model == 1 ? kg_gnp_count(q->undirected, q->n, q->p, q->seed, q->chunks,
+                                                1024, S->d_slots + 2 * r.slot, s)
+                                 : kg_gnp_binomial_count(q->undirected, q->n, q->p, q->seed,
+                                                         q->chunks, S->d_slots + 2 * r.slot, s);
     if (st == KG_OK &&
         cudaMemcpyAsync(S->h_slots + 2 * r.slot, S->d_slots + 2 * r.slot, 8, cudaMemcpyDeviceToHost,
                         s) != cudaSuccess)

@@ -10,7 +10,8 @@ batched_instances(): 4096 independent G(n,m) instances, n log-uniform in
     <= m / 2^16, clamped to [1, min(64, n)] (directed) or [1, min(32, n)].
 serving_requests(): a Poisson stream of requests mixing directed /
     undirected G(n,m) and G(n,p), n log-uniform in [2^10, 2^26], average
-    degree uniform in [4, 32].
+    degree uniform in [4, 32]; G(n,p) requests use the sampler named by
+    gnp_model ("gnp_binomial": binomial chunk counts, "gnp": geometric skips).
 """
 from __future__ import annotations
 
@@ -53,7 +54,8 @@ def instance_entries(inst) -> int:
     return 2 * inst["m"] if inst["undirected"] else inst["m"]
 
 
-def serving_requests(count: int, rate_per_s: float, key: int = KEY_SERVE):
+def serving_requests(count: int, rate_per_s: float, key: int = KEY_SERVE,
+                     gnp_model: str = "gnp_binomial"):
     """Requests with Poisson arrival times (seconds from 0)."""
     rng = np.random.Generator(np.random.Philox(key=key))
     t = 0.0
@@ -66,7 +68,7 @@ def serving_requests(count: int, rate_per_s: float, key: int = KEY_SERVE):
         kind = int(u_kind * 4)  # 0 gnm dir, 1 gnm und, 2 gnp dir, 3 gnp und
         und = kind in (1, 3)
         req = {"id": i, "arrival": t, "n": n, "seed": 1000 + i, "undirected": und,
-               "model": "gnm" if kind < 2 else "gnp"}
+               "model": "gnm" if kind < 2 else gnp_model}
         if kind < 2:
             req["m"] = int(round(d * n / 2)) if und else int(round(d * n))
         else:

@@ -23,11 +23,12 @@ def _small_requests(count, seed=3):
     for i in range(count):
         n = int(2 ** rng.uniform(8, 16))
         d = float(rng.uniform(4, 32))
-        kind = int(rng.integers(0, 4))
-        und = kind in (1, 3)
-        req = {"n": n, "seed": 100 + i, "undirected": und, "model": "gnm" if kind < 2 else "gnp",
+        kind = int(rng.integers(0, 6))
+        und = kind in (1, 3, 5)
+        model = "gnm" if kind < 2 else ("gnp" if kind < 4 else "gnp_binomial")
+        req = {"n": n, "seed": 100 + i, "undirected": und, "model": model,
                "chunks": int(min(n, 1 + rng.integers(0, 16))), "arrival": 0.0}
-        if kind < 2:
+        if model == "gnm":
             pairs = n * (n - 1) // (2 if und else 1)
             req["m"] = min(pairs, int(d * n / (2 if und else 1)))
         else:
@@ -46,6 +47,15 @@ def _alone(kg, req):
         out = torch.empty((max(k, 1), 2), dtype=torch.int32, device="cuda")
         f = kg.kg_gnm_undirected if req["undirected"] else kg.kg_gnm_directed
         f(req["n"], req["m"], req["seed"], req["chunks"], 4, out.data_ptr(), k, s)
+    elif req["model"] == "gnp_binomial":
+        cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+        kg.kg_gnp_binomial_count(req["undirected"], req["n"], req["p"], req["seed"], req["chunks"],
+                                 cnt.data_ptr(), s)
+        k = int(cnt.item())
+        out = torch.empty((max(k, 1), 2), dtype=torch.int32, device="cuda")
+        kg.kg_gnp_binomial(req["undirected"], req["n"], req["p"], req["seed"], req["chunks"], 4,
+                           out.data_ptr(), k, cnt.data_ptr(), s)
+        assert int(cnt.item()) == k
     else:
         cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
         kg.kg_gnp_count(req["undirected"], req["n"], req["p"], req["seed"], req["chunks"], 1024,
