@@ -29,6 +29,11 @@ N_VERT, M_EDGES, P_CHUNKS, SEED = 1 << 36, 1 << 33, 1 << 16, 1
 SLABS = 16
 CHUNKS_PER_SLAB = P_CHUNKS // SLABS
 SLAB_CAP = (1 << 29) + (1 << 21)  # edges per slab buffer (mean 2^29, sd ~2^14.5)
+# DRAM bytes (read + write) per edge of the leaf kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum) of its launch on chunks
+# [0, 256) of this workload (python bench.py --profile-chunks 256):
+# 480,651,520 B / 33,550,402 edges; scaled to a slab launch by its edges.
+LEAF_TRAFFIC_PER_EDGE = (477340672 + 3310848) / 33550402
 ID_BYTES = 8
 WORKLOAD = "directed G(n,m): n=2^36, m=2^33, 2^16 chunks, uint64 ids, 16 slabs of 8 GiB, per-chunk digest + out-degree histogram"
 METRIC = "edges/s (directed G(n,m), n=2^36, m=2^33, 2^16 chunks, uint64 ids, on-device digest)"
@@ -423,7 +428,8 @@ def main():
                    "l2": "no flush: 128 GiB of output per step, far above the 129 MB L2"},
         "write_GBps": M_EDGES * 16 * args.steps / (ms / 1e3) / 1e9,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": LEAF_TRAFFIC_PER_EDGE * M_EDGES / SLABS,
                      "kernel": "leaf_fast_kernel (Floyd draws, shared-memory sort, emit, digest)",
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
         "kernel_ms": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},

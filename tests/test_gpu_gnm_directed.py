@@ -170,3 +170,34 @@ def test_edge_digest_matches_oracle(kg, orc):
     kg.check_device_error()
     u, v = edges_np(t, 8)
     assert int(d.cpu().numpy().view(np.uint64)[0]) == orc.edge_checksum(u, v)
+
+
+@pytest.mark.parametrize("n,m,P,seed", [
+    (2000, 2000 * 1999 // 3, 4, 21),       # rows of ~670 edges: runs across warps and tiles
+    (1 << 16, 1 << 22, 16, 22),            # rows of ~64 edges
+    (1 << 20, 1 << 21, 8, 23),             # rows of ~2 edges
+    (5000, 5000 * 4999 // 2, 3, 24),       # density 1/2: replaced draws in every leaf
+])
+def test_fused_digest_and_histogram_per_chunk(kg, orc, n, m, P, seed):
+    """The digest and out-degree histogram fused into the leaf kernel equal the
+    oracle's checksum and histogram of each chunk, at row lengths from ~2 to
+    ~2500 edges (runs of equal rows crossing warps, tiles and chunks)."""
+    import torch
+    s = kg._stream_ptr(None)
+    counts = torch.zeros(P, dtype=torch.int64, device="cuda")
+    kg.kg_gnm_directed_chunk_counts(n, m, seed, P, counts.data_ptr(), s)
+    cnt = counts.cpu().numpy().view(np.uint64)
+    k = int(cnt.sum())
+    out = torch.empty((k, 2), dtype=torch.int64, device="cuda")
+    dig = torch.zeros(P, dtype=torch.int64, device="cuda")
+    hist = torch.zeros((P, 65), dtype=torch.int64, device="cuda")
+    kg.kg_gnm_directed_range(n, m, seed, P, 0, P, counts.data_ptr(), 8, out.data_ptr(), k,
+                             dig.data_ptr(), hist.data_ptr(), s)
+    kg.check_device_error()
+    gd = dig.cpu().numpy().view(np.uint64)
+    gh = hist.cpu().numpy().view(np.uint64)
+    for c in range(P):
+        ou, ov = orc.gnm_directed_chunk(n, m, seed, P, c, int(cnt[c]))
+        assert int(gd[c]) == orc.edge_checksum(ou, ov), c
+        r0, r1 = c * n // P, (c + 1) * n // P
+        assert np.array_equal(gh[c], orc.outdegree_hist(ou, r0, r1)), c
