@@ -69,6 +69,13 @@ struct DirGeom {
     u = x.r0 + q;
     v = w + (w >= u ? 1 : 0);
   }
+  // first offset and length of the row of `off` (which maps to (u, v))
+  __host__ __device__ __forceinline__ void row_span(const Ctx&, uint64_t off, uint64_t u,
+                                                    uint64_t v, uint64_t& start,
+                                                    uint64_t& len) const {
+    start = off - (v - (v > u ? 1 : 0));
+    len = n - 1;
+  }
 };
 
 // Row of offset `off` in a rectangle of row length sj: off / sj, in 32-bit
@@ -157,6 +164,18 @@ struct UndGeom {
     const uint64_t w = tri_row(off);
     u = x.ri + w;
     v = x.ri + (off - uint64_t(u128(w) * (w - 1) / 2));
+  }
+  // first offset and length of the row of `off` (which maps to (u, v))
+  __host__ __device__ __forceinline__ void row_span(const Ctx& x, uint64_t off, uint64_t u,
+                                                    uint64_t v, uint64_t& start,
+                                                    uint64_t& len) const {
+    if (!x.tri) {
+      start = off - (v - x.rj);
+      len = x.sj;
+    } else {
+      start = off - (v - x.ri);
+      len = u - x.ri;
+    }
   }
 };
 

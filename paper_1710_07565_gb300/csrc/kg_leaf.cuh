@@ -491,56 +491,63 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
     }
     // ---- 7. emit; lane l of warp w takes r = r0 + 32 w + l, so that every
     // warp holds 32 consecutive sorted edges.  DIGEST: the order-independent
-    // digest, and the runs of equal rows u (A[r] is overwritten by u): a run
-    // starts where u differs from its predecessor (neighbours by warp
-    // shuffles, A across warps); a run longer than one is measured by a scan
-    // of A from its start.
+    // digest, and the runs of equal rows u.  Offset x is in the row of x' < x
+    // iff lo + x' >= the first offset of x's row, and x'' > x is iff
+    // lo + x'' < that row's end (Geom::row_span); the neighbours' offsets come
+    // by shuffles (from A across warps), so no division, no barrier and no
+    // stored rows are needed; a run longer than one is measured by a scan of
+    // A from its start.
     unsigned long long dsum = 0;
     uint32_t c1 = 0, nr = 0;
     const uint64_t lo = td.lo, base = td.base;
     const typename Geom::Ctx gx = td.gx;
     const int lane = tid & 31;
-    for (uint32_t r = tid; r < k; r += FAST_THREADS) {
-      uint64_t u, v;
-      g.map(gx, lo + res[r], u, v);
-      sink.put(base + r, u, v);
-      if (DIGEST) {
-        dsum += edge_hash(u, v);
-        res[r] = u;
+    if constexpr (!DIGEST) {
+      for (uint32_t r = tid; r < k; r += FAST_THREADS) {
+        uint64_t u, v;
+        g.map(gx, lo + res[r], u, v);
+        sink.put(base + r, u, v);
       }
-    }
-    if (DIGEST) {
-      __syncthreads();
+    } else {
       for (uint32_t r0 = 0; r0 < k; r0 += FAST_THREADS) {  // uniform over the block
         const uint32_t r = r0 + tid;
         const bool in = r < k;
-        const uint64_t u = in ? res[r] : ~uint64_t(0) - 1;
-        uint64_t prev = __shfl_up_sync(0xffffffffu, u, 1);
-        uint64_t next = __shfl_down_sync(0xffffffffu, u, 1);
-        if (lane == 0) prev = (in && r > 0) ? res[r - 1] : ~uint64_t(0);
-        if (lane == 31) next = (r + 1 < k) ? res[r + 1] : ~uint64_t(0);
-        if (in && (r == 0 || u != prev)) {  // a run of rows u starts at r
-          uint32_t len = 1;
-          if (r + 1 < k && u == next) {
-            uint32_t q = r + 2;
-            while (q < k && res[q] == u) ++q;
-            len = q - r;
-          }
-          ++nr;
-          const bool first = (r == 0), last = (r + len == k);
-          if (first) {
-            s_fu = u;
-            s_fl = len;
-          }
-          if (last) {
-            s_lu = u;
-            s_ll = len;
-          }
-          if (!first && !last) {
-            if (len == 1)
-              ++c1;
-            else
-              atomicAdd(&bh[len < 64 ? len : 64], 1u);
+        const uint64_t x = in ? res[r] : 0;
+        uint64_t xp = __shfl_up_sync(0xffffffffu, x, 1);
+        uint64_t xn = __shfl_down_sync(0xffffffffu, x, 1);
+        if (lane == 0 && in && r > 0) xp = res[r - 1];
+        if (lane == 31 && r + 1 < k) xn = res[r + 1];
+        if (in) {
+          uint64_t u, v;
+          g.map(gx, lo + x, u, v);
+          sink.put(base + r, u, v);
+          dsum += edge_hash(u, v);
+          uint64_t rs, rl;  // the row's first offset and its length
+          g.row_span(gx, lo + x, u, v, rs, rl);
+          if (r == 0 || lo + xp < rs) {  // a run of row u starts at r
+            const uint64_t re = rs + rl;
+            uint32_t len = 1;
+            if (r + 1 < k && lo + xn < re) {
+              uint32_t q = r + 2;
+              while (q < k && lo + res[q] < re) ++q;
+              len = q - r;
+            }
+            ++nr;
+            const bool first = (r == 0), last = (r + len == k);
+            if (first) {
+              s_fu = u;
+              s_fl = len;
+            }
+            if (last) {
+              s_lu = u;
+              s_ll = len;
+            }
+            if (!first && !last) {
+              if (len == 1)
+                ++c1;
+              else
+                atomicAdd(&bh[len < 64 ? len : 64], 1u);
+            }
           }
         }
       }
