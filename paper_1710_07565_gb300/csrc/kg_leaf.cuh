@@ -524,16 +524,16 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
           dsum += edge_hash(u, v);
           uint64_t rs, rl;  // the row's first offset and its length
           g.row_span(gx, lo + x, u, v, rs, rl);
-          if (r == 0 || lo + xp < rs) {  // a run of row u starts at r
-            const uint64_t re = rs + rl;
-            uint32_t len = 1;
-            if (r + 1 < k && lo + xn < re) {
-              uint32_t q = r + 2;
-              while (q < k && lo + res[q] < re) ++q;
-              len = q - r;
-            }
-            ++nr;
-            const bool first = (r == 0), last = (r + len == k);
+          const uint64_t re = rs + rl;
+          const bool st = r == 0 || lo + xp < rs;     // a run of row u starts at r
+          const bool en = r + 1 == k || lo + xn >= re;  // ... and ends at r
+          nr += st;
+          c1 += st & en & (r != 0) & (r + 1 != k);     // one-edge runs inside the tile
+          if (st & !en) {  // a run of two or more edges (rare when rows are sparse)
+            uint32_t q = r + 2;
+            while (q < k && lo + res[q] < re) ++q;
+            const uint32_t len = q - r;
+            const bool first = (r == 0), last = (q == k);
             if (first) {
               s_fu = u;
               s_fl = len;
@@ -542,11 +542,15 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
               s_lu = u;
               s_ll = len;
             }
-            if (!first && !last) {
-              if (len == 1)
-                ++c1;
-              else
-                atomicAdd(&bh[len < 64 ? len : 64], 1u);
+            if (!first && !last) atomicAdd(&bh[len < 64 ? len : 64], 1u);
+          } else if (st & ((r == 0) | (r + 1 == k))) {  // a one-edge run at a tile end
+            if (r == 0) {
+              s_fu = u;
+              s_fl = 1;
+            }
+            if (r + 1 == k) {
+              s_lu = u;
+              s_ll = 1;
             }
           }
         }
