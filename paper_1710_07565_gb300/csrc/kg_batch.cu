@@ -11,12 +11,14 @@
 #include "kg.h"
 #include "kg_run.cuh"
 #include "kg_und.cuh"
+#include "kg_assemble.cuh"
 
 namespace kg {
 
 struct BInst {
   uint64_t n, m, seed;
   uint32_t P, undirected;
+  uint32_t big, pad_;  // big: an undirected instance assembled by the per-instance sequence
   int d, D;
   uint64_t C;
   uint64_t chunk_base, tile_base, sample_base, pair_base, vert_base, out_base;
@@ -359,8 +361,9 @@ __global__ void batch_und_degree(const BInst* __restrict__ inst, uint32_t count,
   for (uint64_t p0 = uint64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); p0 < npairs;
        p0 += uint64_t(gridDim.x) * blockDim.x) {  // uniform over the warp
     const uint64_t p = p0 + lane;
-    const uint64_t vb = inst[warp_find_inst(inst, count, p < npairs ? p : npairs - 1, 1, lane)].vert_base;
-    if (p < npairs) {
+    const BInst& I = inst[warp_find_inst(inst, count, p < npairs ? p : npairs - 1, 1, lane)];
+    if (p < npairs && !I.big) {
+      const uint64_t vb = I.vert_base;
       atomicAdd(&deg[vb + pairs[2 * p]], 1ull);
       atomicAdd(&deg[vb + pairs[2 * p + 1]], 1ull);
     }
@@ -386,16 +389,15 @@ __global__ void batch_und_scatter(const BInst* __restrict__ inst, uint32_t count
   for (uint64_t p0 = uint64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); p0 < npairs;
        p0 += uint64_t(gridDim.x) * blockDim.x) {  // uniform over the warp
     const uint64_t p = p0 + lane;
-    const uint64_t vb = inst[warp_find_inst(inst, count, p < npairs ? p : npairs - 1, 1, lane)].vert_base;
-    if (p >= npairs) continue;
+    const BInst& I = inst[warp_find_inst(inst, count, p < npairs ? p : npairs - 1, 1, lane)];
+    if (p >= npairs || I.big) continue;
+    const uint64_t vb = I.vert_base;
     const uint32_t u = pairs[2 * p], v = pairs[2 * p + 1];
     const uint64_t a = atomicAdd(&cursor[vb + u], 1ull);
     const uint64_t b = atomicAdd(&cursor[vb + v], 1ull);
     if (a < cap && b < cap) {
-      out[2 * a] = u;
-      out[2 * a + 1] = v;
-      out[2 * b] = v;
-      out[2 * b + 1] = u;
+      reinterpret_cast<uint2*>(out)[a] = make_uint2(u, v);
+      reinterpret_cast<uint2*>(out)[b] = make_uint2(v, u);
     } else {
       set_error(err, ST_CAPACITY);
     }
@@ -501,11 +503,21 @@ struct BatchPlan {
   uint64_t* rowptr;
   void* arena;
   size_t arena_bytes;
+  // undirected instances of at least BIG_PAIRS pairs: assembled one by one
+  // with the per-instance sequence (scratch carved from big_arena each time)
+  struct Big {
+    uint64_t n, m, pair_base, out_base;
+  };
+  std::vector<Big> bigs;
+  void* big_arena = nullptr;
+  size_t big_arena_bytes = 0;
   // launch shapes chosen by kg_batch_tune (they do not change the output)
   unsigned tree_threads = 256;
   unsigned leaf_grid_cap = 0x7fffffffu;
   std::vector<void*> allocs;
 };
+
+constexpr uint64_t BIG_PAIRS = uint64_t(1) << 20;
 
 static uint64_t piece(uint64_t b) { return (b + 255) & ~uint64_t(255); }
 static uint64_t scan_scratch(uint64_t n) {
@@ -596,9 +608,21 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
                                                                   bp->long_rows, bp->nlong);
     if (launch_ok()) return ST_CUDA;
   }
-  ProfScope ps(PROF_ASSEMBLY, s);
-  batch_und_sort_long<<<152 * 2, 256, 0, s>>>(bp->rowpos, bp->deg, out, bp->long_rows, bp->nlong);
-  return launch_ok();
+  {
+    ProfScope ps(PROF_ASSEMBLY, s);
+    batch_und_sort_long<<<152 * 2, 256, 0, s>>>(bp->rowpos, bp->deg, out, bp->long_rows,
+                                                bp->nlong);
+    if (launch_ok()) return ST_CUDA;
+  }
+  // the big undirected instances, one after the other, each by the
+  // per-instance assembly over its slices (the scratch is reused in stream order)
+  for (const auto& g : bp->bigs) {
+    Workspace wb(s, bp->big_arena, bp->big_arena_bytes);
+    st = assemble<uint32_t>(bp->pairs_buf + 2 * g.pair_base, nullptr, g.m, g.n,
+                            out + 2 * g.out_base, 2 * g.m, wb, s, err);
+    if (st) return st;
+  }
+  return ST_OK;
 }
 
 }  // namespace kg
@@ -660,6 +684,9 @@ kg_status kg_batch_create(const kg_instance* h_inst, uint32_t count, int id_byte
     I.pair_base = pairs;
     I.vert_base = verts;
     I.out_base = entries;
+    I.big = (I.undirected && q.m >= BIG_PAIRS) ? 1u : 0u;
+    I.pad_ = 0;
+    if (I.big) bp.bigs.push_back({q.n, q.m, pairs, entries});
     bp.out_offsets[i] = entries;
     chunks += I.C;
     tiles += I.C << I.d;
@@ -722,6 +749,14 @@ kg_status kg_batch_create(const kg_instance* h_inst, uint32_t count, int id_byte
   bp.nlong = static_cast<unsigned long long*>(p);
   bp.arena_bytes = scan_scratch(tiles) + scan_scratch(verts) + 512;  // both scans of one run
   A(&bp.arena, bp.arena_bytes);
+  // scratch of the per-instance assembly (deg, rowptr, cursor, long rows, count, scan)
+  uint64_t nbig = 0;
+  for (const auto& g : bp.bigs) nbig = std::max(nbig, g.n);
+  if (nbig) {
+    bp.big_arena_bytes = 3 * piece(nbig * 8) + piece((nbig + 1) * 8) + piece(8) +
+                         scan_scratch(nbig) + 512;
+    A(&bp.big_arena, bp.big_arena_bytes);
+  }
   if (!st && cudaMemcpy(bp.inst, tab.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice) !=
                  cudaSuccess)
     st = ST_CUDA;

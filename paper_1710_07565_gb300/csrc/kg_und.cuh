@@ -132,6 +132,15 @@ __device__ __forceinline__ void load_pair(const Id* p, uint64_t i, uint64_t& u, 
   v = p[2 * i + 1];
 }
 
+// one 8- or 16-byte store of the pair (u, v) at slot i
+template <class Id>
+__device__ __forceinline__ void store_pair(Id* out, uint64_t i, uint64_t u, uint64_t v) {
+  if (sizeof(Id) == 4)
+    reinterpret_cast<uint2*>(out)[i] = make_uint2(uint32_t(u), uint32_t(v));
+  else
+    reinterpret_cast<ulonglong2*>(out)[i] = make_ulonglong2(u, v);
+}
+
 template <class Id>
 __global__ void und_degree(const Id* __restrict__ pairs, const uint64_t* __restrict__ npairs_dev,
                            uint64_t npairs_host, unsigned long long* __restrict__ deg) {
@@ -157,14 +166,12 @@ __global__ void und_scatter(const Id* __restrict__ pairs, const uint64_t* __rest
     const uint64_t p = atomicAdd(&cursor[u], 1ull);
     const uint64_t q = atomicAdd(&cursor[v], 1ull);
     if (p < cap) {
-      out[2 * p] = Id(u);
-      out[2 * p + 1] = Id(v);
+      store_pair(out, p, u, v);
     } else {
       set_error(err, ST_CAPACITY);
     }
     if (q < cap) {
-      out[2 * q] = Id(v);
-      out[2 * q + 1] = Id(u);
+      store_pair(out, q, v, u);
     } else {
       set_error(err, ST_CAPACITY);
     }
