@@ -99,24 +99,47 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(seconds=10.0, min_chunks=16):
-    """The oracle, single-threaded, on a bounded sample: whole chunks of the
-    workload (chunk tree + chunk edges + digest + histogram), until ~seconds."""
+def _oracle_chunks(job):
+    """One worker of the CPU baseline: whole chunks of the workload, generated
+    with the oracle (edges, digest, histogram) until the time budget is spent."""
     import oracle
+    cnt, start, stride, seconds = job
     t0 = time.perf_counter()
-    cnt = oracle.gnm_directed_chunk_counts(N_VERT, M_EDGES, SEED, P_CHUNKS)
-    edges, chunks = 0, 0
-    while chunks < min_chunks or time.perf_counter() - t0 < seconds:
-        c = (chunks * 7919) % P_CHUNKS
+    edges, chunks, i = 0, 0, start
+    while chunks < 1 or time.perf_counter() - t0 < seconds:
+        c = (i * 7919) % P_CHUNKS
         u, v = oracle.gnm_directed_chunk(N_VERT, M_EDGES, SEED, P_CHUNKS, c, int(cnt[c]))
         oracle.edge_checksum(u, v)
         oracle.outdegree_hist(u, c * N_VERT // P_CHUNKS, (c + 1) * N_VERT // P_CHUNKS)
         edges += len(u)
         chunks += 1
+        i += stride
+    return edges, chunks
+
+
+def cpu_baseline(seconds=10.0, workers=None):
+    """The oracle as it stands, on a bounded sample of the workload: the chunk
+    split tree of all 2^16 chunks, then whole chunks generated chunk-parallel
+    by one process per host core (spawned: this process holds a CUDA context)
+    until ~seconds of wall time."""
+    import multiprocessing as mp
+
+    import oracle
+    oracle.build()
+    workers = workers or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    cnt = oracle.gnm_directed_chunk_counts(N_VERT, M_EDGES, SEED, P_CHUNKS)
+    t_tree = time.perf_counter() - t0
+    jobs = [(cnt, w, workers, max(seconds - t_tree, 0.5)) for w in range(workers)]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        res = pool.map(_oracle_chunks, jobs)
     dt = time.perf_counter() - t0
-    return {"value": edges / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
-            "sample": f"chunk split tree of all 2^16 chunks + {chunks} whole chunks "
-                      f"({edges} edges) with digest and histogram, {dt:.1f} s single-threaded"}
+    edges = sum(r[0] for r in res)
+    chunks = sum(r[1] for r in res)
+    return {"value": edges / dt, "unit": "edges/s", "cores": workers, "kind": "oracle",
+            "sample": f"chunk split tree of all 2^16 chunks ({t_tree:.2f} s, one core) + "
+                      f"{chunks} whole chunks ({edges} edges) with digest and histogram, "
+                      f"chunk-parallel on {workers} processes, {dt:.1f} s wall"}
 
 
 def run_reference(args, rank, world):
@@ -124,9 +147,9 @@ def run_reference(args, rank, world):
         return
     steps = []
     for _ in range(args.warmup):
-        cpu_baseline(seconds=2.0, min_chunks=4)
+        cpu_baseline(seconds=2.0)
     for _ in range(args.steps):
-        steps.append(cpu_baseline(seconds=args.ref_seconds, min_chunks=8))
+        steps.append(cpu_baseline(seconds=args.ref_seconds))
     val = statistics.median(s["value"] for s in steps)
     cb = dict(steps[-1])
     cb["value"] = val
@@ -275,6 +298,17 @@ def other_workloads(kg, serve_requests=1000):
         "entries_per_s": ent / dt2, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(0.99 * (len(lat) - 1))],
         "ok": all(r["status"] == 0 for r in done),
         "sample": f"first {len(reqs)} requests of the seeded 100k-request stream"}
+    # the same stream at 0.5x and 1.0x of the closed-loop capacity (first half)
+    for frac in (0.5, 1.0):
+        rq = workloads.serving_requests(serve_requests // 2, frac * cap_rps)
+        t0 = time.perf_counter()
+        dn = kg.serve(rq, budget, streams=8, realtime=True)
+        dt3 = time.perf_counter() - t0
+        lt = sorted(r["t_done_ms"] - r["t_submit_ms"] for r in dn)
+        res["serving"][f"at_{frac:.1f}x"] = {
+            "requests": len(rq), "rate_per_s": frac * cap_rps, "requests_per_s": len(rq) / dt3,
+            "p50_ms": lt[len(lt) // 2], "p99_ms": lt[int(0.99 * (len(lt) - 1))],
+            "ok": all(r["status"] == 0 for r in dn)}
     return res
 
 
