@@ -95,6 +95,9 @@ def lib():
             L.or_gnm_undirected.restype = i32
             L.or_gnp.argtypes = [i32, u64, dbl, u64, u32, u32, p64, p64, u64, p64]
             L.or_gnp.restype = i32
+            L.or_gnm_undirected_rows.argtypes = [u64, u64, u64, u32, u32, u32, u32, u32, p64, p64,
+                                                 u64, p64]
+            L.or_gnm_undirected_rows.restype = i32
             L.or_gnp_binomial_counts.argtypes = [i32, u64, dbl, u64, u32, p64]
             L.or_gnp_binomial_counts.restype = i32
             L.or_gnp_binomial.argtypes = [i32, u64, dbl, u64, u32, u32, u32, p64, p64, u64, p64]
@@ -231,6 +234,23 @@ def gnp(undirected, n, p, seed, P, k_leaf=K_LEAF, cap_hint=None):
             cap = cnt.value
             continue
         _check(rc, "gnp")
+        return u[:cnt.value], v[:cnt.value]
+
+
+def gnm_undirected_rows(n, m, seed, P, b0, b1, k_leaf=K_LEAF, k_max=K_MAX, cap_hint=None):
+    """Rows of row blocks [b0, b1) of undirected G(n,m), both directions (Sec. 4.2)."""
+    L = lib()
+    cap = cap_hint if cap_hint is not None else 1 << 16
+    while True:
+        u = np.zeros(max(cap, 1), dtype=np.uint64)
+        v = np.zeros(max(cap, 1), dtype=np.uint64)
+        cnt = ctypes.c_uint64()
+        rc = L.or_gnm_undirected_rows(n, m, seed, P, k_leaf, k_max, b0, b1, _p64(u), _p64(v), cap,
+                                      ctypes.byref(cnt))
+        if rc == 3:
+            cap = cnt.value
+            continue
+        _check(rc, "gnm_undirected_rows")
         return u[:cnt.value], v[:cnt.value]
 
 

@@ -619,6 +619,59 @@ int or_gnm_undirected(uint64_t n, uint64_t m, uint64_t seed, uint32_t P, uint32_
     return rc;
 }
 
+/* Rows of the row blocks [b0, b1) of the undirected graph, both directions,
+ * sorted by (u, v): the entries (u, v) of the chunks (i, j <= i) of those row
+ * blocks, and the mirrored entries (v, u) of the chunks (i >= j, j) of those
+ * column blocks -- the chunks a PE of Sec. 4.2 regenerates from their shared
+ * seeds.  Concatenated over all blocks this is or_gnm_undirected's list. */
+int or_gnm_undirected_rows(uint64_t n, uint64_t m, uint64_t seed, uint32_t P, uint32_t k_leaf,
+                           uint32_t k_max, uint32_t b0, uint32_t b1, uint64_t *u, uint64_t *v,
+                           uint64_t cap, uint64_t *count)
+{
+    int rc = check_undirected(n, m, P);
+    if (rc)
+        return rc;
+    if (k_leaf < 2 || k_max < k_leaf || b0 >= b1 || b1 > P)
+        return 1;
+    uint64_t *cnt = (uint64_t *)malloc((uint64_t)P * P * sizeof(uint64_t));
+    if (!cnt)
+        return 1;
+    rc = or_gnm_undirected_chunk_counts(n, m, seed, P, cnt);
+    u128 rmax = ((u128)n + P - 1) / P;
+    int d = 0;
+    if (!rc)
+        rc = tile_depth(m, rmax * rmax, tri_pairs(n), k_leaf, &d);
+    uint64_t lo = row_bound(n, P, b0), hi = row_bound(n, P, b1);
+    edge_buf b = {0, 0, 0, 0};
+    for (uint32_t i = 0; !rc && i < P; i++)
+        for (uint32_t j = 0; !rc && j <= i; j++) {
+            if (!((i >= b0 && i < b1) || (j >= b0 && j < b1)))
+                continue;
+            uint64_t kc = cnt[(uint64_t)i * P + j];
+            uint64_t *offs = (uint64_t *)malloc((kc ? kc : 1) * sizeof(uint64_t));
+            if (!offs) {
+                rc = 1;
+                break;
+            }
+            rc = chunk_offsets(seed, (uint64_t)i * P + j, und_chunk_universe(n, P, i, j), d, k_max,
+                               kc, offs);
+            for (uint64_t t = 0; !rc && t < kc; t++) {
+                uint64_t uu, vv;
+                und_map(n, P, i, j, offs[t], &uu, &vv);
+                if (uu >= lo && uu < hi)
+                    eb_push(&b, uu, vv);
+                if (vv >= lo && vv < hi)
+                    eb_push(&b, vv, uu);
+            }
+            free(offs);
+        }
+    free(cnt);
+    if (!rc)
+        rc = finish_sorted(&b, u, v, cap, count);
+    free(b.e);
+    return rc;
+}
+
 /* ---------------- G(n,p), Sec. 4.3 ---------------- */
 
 /* Tile length T = the largest power of two <= max(1, k_leaf / p), capped at 2^62. */

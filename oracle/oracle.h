@@ -60,6 +60,12 @@ int or_gnm_undirected_chunk_counts(uint64_t n, uint64_t m, uint64_t seed, uint32
 int or_gnm_undirected(uint64_t n, uint64_t m, uint64_t seed, uint32_t P,
                       uint32_t k_leaf, uint32_t k_max, uint64_t *u, uint64_t *v);
 
+/* the rows of row blocks [b0, b1) of the same undirected graph (both directions),
+ * from the chunks of those row and column blocks (Sec. 4.2); *count = entries */
+int or_gnm_undirected_rows(uint64_t n, uint64_t m, uint64_t seed, uint32_t P, uint32_t k_leaf,
+                           uint32_t k_max, uint32_t b0, uint32_t b1, uint64_t *u, uint64_t *v,
+                           uint64_t cap, uint64_t *count);
+
 /* ---- G(n,p), Sec. 4.3 (geometric skips); *count = number of entries ---- */
 int or_gnp(int undirected, uint64_t n, double p, uint64_t seed, uint32_t P,
            uint32_t k_leaf, uint64_t *u, uint64_t *v, uint64_t cap, uint64_t *count);

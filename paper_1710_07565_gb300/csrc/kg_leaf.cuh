@@ -493,10 +493,9 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
     // warp holds 32 consecutive sorted edges.  DIGEST: the order-independent
     // digest, and the runs of equal rows u.  Offset x is in the row of x' < x
     // iff lo + x' >= the first offset of x's row, and x'' > x is iff
-    // lo + x'' < that row's end (Geom::row_span); the neighbours' offsets come
-    // by shuffles (from A across warps), so no division, no barrier and no
-    // stored rows are needed; a run longer than one is measured by a scan of
-    // A from its start.
+    // lo + x'' < that row's end (Geom::row_span); the neighbours' offsets are
+    // read from A, so no division, no barrier and no stored rows are needed;
+    // a run longer than one is measured by a scan of A from its start.
     unsigned long long dsum = 0;
     uint32_t c1 = 0, nr = 0;
     const uint64_t lo = td.lo, base = td.base;
@@ -513,10 +512,8 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
         const uint32_t r = r0 + tid;
         const bool in = r < k;
         const uint64_t x = in ? res[r] : 0;
-        uint64_t xp = __shfl_up_sync(0xffffffffu, x, 1);
-        uint64_t xn = __shfl_down_sync(0xffffffffu, x, 1);
-        if (lane == 0 && in && r > 0) xp = res[r - 1];
-        if (lane == 31 && r + 1 < k) xn = res[r + 1];
+        const uint64_t xp = (in && r > 0) ? res[r - 1] : 0;  // the neighbours' offsets
+        const uint64_t xn = (r + 1 < k) ? res[r + 1] : 0;
         if (in) {
           uint64_t u, v;
           g.map(gx, lo + x, u, v);

@@ -251,6 +251,28 @@ def test_gnp_extremes(orc):
     check_simple(u, v, 7, directed=False)
 
 
+@pytest.mark.parametrize("n,m,P,k_leaf,k_max,splits", [
+    (40, 300, 5, 4, 6, [0, 2, 3, 5]),
+    (1000, 20000, 7, 1024, 2048, [0, 1, 4, 7]),
+    (5000, 5000 * 4999 // 4, 4, 1024, 2048, [0, 2, 4]),   # rows of ~2500 entries
+    (333, 1000, 333, 8, 16, [0, 100, 101, 333]),          # one vertex per block
+])
+def test_undirected_row_blocks_concatenate_to_the_graph(orc, n, m, P, k_leaf, k_max, splits):
+    """Sec. 4.2: a PE that regenerates the chunks of its row and column blocks
+    produces exactly its rows of the one graph; the row ranges concatenate to
+    the full list in both directions."""
+    fu, fv = orc.gnm_undirected(n, m, 3, P, k_leaf, k_max)
+    parts_u, parts_v = [], []
+    for b0, b1 in zip(splits[:-1], splits[1:]):
+        u, v = orc.gnm_undirected_rows(n, m, 3, P, b0, b1, k_leaf, k_max)
+        lo, hi = b0 * n // P, b1 * n // P
+        assert np.all((u >= lo) & (u < hi))
+        parts_u.append(u)
+        parts_v.append(v)
+    assert np.array_equal(np.concatenate(parts_u), fu)
+    assert np.array_equal(np.concatenate(parts_v), fv)
+
+
 # ------------------------------------------- G(n,p) by binomial chunk counts
 
 def _graph_law(orc_fn, undirected, n, p, S):
