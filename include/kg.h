@@ -109,6 +109,31 @@ kg_status kg_gnm_undirected_ex(uint64_t n, uint64_t m, uint64_t seed, uint32_t c
                                uint64_t cap_edges, void* stream);
 
 /*
+ * Undirected G(n,m) by row blocks, Sec. 4.2 at scale: the graph of
+ * kg_gnm_undirected (same n, m, seed, chunks; default leaf sizes), but only
+ * the rows of row blocks [b_begin, b_end) -- every entry (u, v) with
+ * floor(b_begin n / P) <= u < floor(b_end n / P), both directions, sorted by
+ * (u, v).  As a PE of the paper does, the call regenerates from their shared
+ * seeds the chunks of those row blocks and of those column blocks, so
+ * consecutive ranges concatenate to the whole list and no range needs another.
+ *   n <= 2^40, ceil(n / chunks) < 2^32, 1 <= chunks <= min(n, 2^16), m <= 2^44,
+ *   m <= n(n-1)/2; id_bytes 4 needs n <= 2^32; 0 <= b_begin < b_end <= chunks.
+ * d_counts: the chunk counts of kg_gnm_undirected_chunk_counts (device,
+ * P(P+1)/2 uint64 in the order k = i(i+1)/2 + j), or NULL to draw them here.
+ * *d_entries (device, optional) receives the number of entries; beyond
+ * cap_edges the device error word becomes KG_ERR_CAPACITY.  Optional per
+ * row block of the range: d_block_digest[b - b_begin], the order-independent
+ * digest of its entries, and d_block_hist[(b - b_begin) * 65 + d], the number
+ * of its rows with degree d (d >= 64 in the last bin).
+ */
+kg_status kg_gnm_undirected_chunk_counts(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                                         uint64_t* d_counts, void* stream);
+kg_status kg_gnm_undirected_rows(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                                 uint32_t b_begin, uint32_t b_end, const uint64_t* d_counts,
+                                 int id_bytes, void* d_out, uint64_t cap_edges, uint64_t* d_entries,
+                                 uint64_t* d_block_digest, uint64_t* d_block_hist, void* stream);
+
+/*
  * G(n,p), Sec. 4.3: every pair independently with probability p, by
  * geometric skips (Batagelj and Brandes, Sec. 3.1) over tiles of each chunk;
  * a tile's skips come from the stream of (chunk id, tile), so the chunk law is

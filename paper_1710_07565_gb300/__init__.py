@@ -61,6 +61,9 @@ def lib() -> ctypes.CDLL:
                 "kg_gnp_undirected": [u64, dbl, u64, u32, i32, vp, u64, vp, vp],
                 "kg_gnp_ex": [i32, u64, dbl, u64, u32, u32, i32, vp, u64, vp, vp],
                 "kg_gnp_binomial": [i32, u64, dbl, u64, u32, i32, vp, u64, vp, vp],
+                "kg_gnm_undirected_chunk_counts": [u64, u64, u64, u32, vp, vp],
+                "kg_gnm_undirected_rows": [u64, u64, u64, u32, u32, u32, vp, i32, vp, u64, vp, vp,
+                                           vp, vp],
                 "kg_gnp_binomial_count": [i32, u64, dbl, u64, u32, vp, vp],
                 "kg_edge_digest": [vp, u64, i32, vp, vp],
                 "kg_last_error": [vp],
@@ -176,6 +179,16 @@ def kg_gnp_undirected(n, p, seed, chunks, id_bytes, d_out, cap_edges, d_count, s
 def kg_gnp_ex(undirected, n, p, seed, chunks, k_leaf, id_bytes, d_out, cap_edges, d_count, stream):
     return _call("kg_gnp_ex", int(undirected), n, p, seed, chunks, k_leaf, id_bytes, d_out,
                  cap_edges, d_count, stream)
+
+
+def kg_gnm_undirected_chunk_counts(n, m, seed, chunks, d_counts, stream):
+    return _call("kg_gnm_undirected_chunk_counts", n, m, seed, chunks, d_counts, stream)
+
+
+def kg_gnm_undirected_rows(n, m, seed, chunks, b_begin, b_end, d_counts, id_bytes, d_out,
+                           cap_edges, d_entries, d_block_digest, d_block_hist, stream):
+    return _call("kg_gnm_undirected_rows", n, m, seed, chunks, b_begin, b_end, d_counts, id_bytes,
+                 d_out, cap_edges, d_entries, d_block_digest, d_block_hist, stream)
 
 
 def kg_gnp_binomial(undirected, n, p, seed, chunks, id_bytes, d_out, cap_edges, d_count, stream):

@@ -1,5 +1,7 @@
 // C ABI: undirected G(n,m) (Sec. 4.2) and G(n,p) (Sec. 4.3), directed and
 // undirected, with the assembly of undirected output in both directions.
+#include <vector>
+
 #include "kg.h"
 #include "kg_gnp.cuh"
 #include "kg_run.cuh"
@@ -18,8 +20,10 @@ struct UndParams {
   int d, D;
 };
 
+// windowed: the caller assembles only a window of rows (kg_gnm_undirected_rows),
+// so n is limited by the chunk sizes instead of by whole-graph row arrays.
 static int check_undirected(uint64_t n, uint64_t m, uint32_t P, uint32_t k_leaf, uint32_t k_max,
-                            int id_bytes, UndParams& up) {
+                            int id_bytes, UndParams& up, bool windowed = false) {
   if (n == 0 || P == 0 || uint64_t(P) > n) return ST_ARG;
   if (id_bytes != 4 && id_bytes != 8) return ST_ARG;
   if (k_leaf < 2 || k_max < k_leaf || k_max > uint32_t(K_MAX)) return ST_ARG;
@@ -28,8 +32,11 @@ static int check_undirected(uint64_t n, uint64_t m, uint32_t P, uint32_t k_leaf,
   up.P = P;
   up.Ntot = tri_pairs(n);
   if (u128(m) > up.Ntot) return ST_ARG;
-  if (m > M_MAX || P > 65536u || n > (uint64_t(1) << 31)) return ST_RANGE;
+  if (m > M_MAX || P > 65536u) return ST_RANGE;
+  if (windowed ? (n > (uint64_t(1) << 40)) : (n > (uint64_t(1) << 31))) return ST_RANGE;
+  if (id_bytes == 4 && n > (uint64_t(1) << 32)) return ST_RANGE;
   const u128 rmax = (u128(n) + P - 1) / P;
+  if (rmax >> 32) return ST_RANGE;
   up.Unom = rmax * rmax;
   int st = tile_depth(m, up.Unom, up.Ntot, k_leaf, up.d);
   if (st) return st;
@@ -76,6 +83,105 @@ static int gnm_undirected_impl(const UndParams& up, uint64_t seed, uint32_t k_ma
   st = run_chunks(g, 0, C, chunk_cnt, up.d, k_max, seed, int(sizeof(Id)), pairs, up.m, ws, s, err);
   if (st) return st;
   return assemble<Id>(pairs, nullptr, up.m, up.n, static_cast<Id*>(d_out), cap, ws, s, err);
+}
+
+// ---------------------------------------------------------------- undirected rows by blocks
+// The chunks (i, j <= i) a range of row blocks needs (Sec. 4.2: a PE
+// regenerates the chunks of its row and of its column), given as a device
+// list of chunk indices k = i(i+1)/2 + j in increasing order.
+struct UndListGeom {
+  UndGeom base;
+  const uint64_t* list;
+  using Ctx = UndGeom::Ctx;
+  __device__ __forceinline__ uint64_t chunk_id(uint64_t c) const { return base.chunk_id(list[c]); }
+  __device__ __forceinline__ uint64_t rows(uint64_t c) const { return base.rows(list[c]); }
+  __device__ __forceinline__ uint64_t universe(uint64_t c) const { return base.universe(list[c]); }
+  __device__ __forceinline__ Ctx ctx(uint64_t c) const { return base.ctx(list[c]); }
+  __device__ __forceinline__ void map(const Ctx& x, uint64_t off, uint64_t& u, uint64_t& v) const {
+    base.map(x, off, u, v);
+  }
+  __device__ __forceinline__ void row_span(const Ctx& x, uint64_t off, uint64_t u, uint64_t v,
+                                           uint64_t& start, uint64_t& len) const {
+    base.row_span(x, off, u, v, start, len);
+  }
+};
+
+__global__ void gather_counts(const uint64_t* __restrict__ src, const uint64_t* __restrict__ idx,
+                              uint64_t n, uint64_t* __restrict__ dst) {
+  for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+       i += uint64_t(gridDim.x) * blockDim.x)
+    dst[i] = src[idx[i]];
+}
+
+// the pairs actually in the buffer: min(total, cap)
+__global__ void clamp_count(const uint64_t* total, uint64_t cap, uint64_t* out) {
+  *out = *total < cap ? *total : cap;
+}
+
+template <class Id>
+static int gnm_undirected_rows_impl(const UndParams& up, uint64_t seed, uint32_t b0, uint32_t b1,
+                                    const uint64_t* d_counts, void* d_out, uint64_t cap,
+                                    uint64_t* d_entries, uint64_t* d_digest, uint64_t* d_hist,
+                                    cudaStream_t s, int* err) {
+  Workspace ws(s);
+  const uint32_t P = up.P;
+  const uint64_t C = uint64_t(P) * (P + 1) / 2;
+  int st;
+  if (!d_counts) {
+    uint64_t* c2 = ws.alloc<uint64_t>(C);
+    if (!ws.ok()) return ST_CUDA;
+    if ((st = run_quadtree(up, seed, c2, ws, s, err))) return st;
+    d_counts = c2;
+  }
+  std::vector<uint64_t> list;
+  for (uint64_t i = 0; i < P; ++i)
+    for (uint64_t j = 0; j <= i; ++j)
+      if ((i >= b0 && i < b1) || (j >= b0 && j < b1)) list.push_back(i * (i + 1) / 2 + j);
+  const uint64_t L = list.size();
+  uint64_t* dlist = ws.alloc<uint64_t>(L);
+  uint64_t* cnt = ws.alloc<uint64_t>(L);
+  uint64_t* off = ws.alloc<uint64_t>(L + 1);
+  uint64_t* npairs = ws.alloc<uint64_t>(1);
+  Id* pairs = ws.alloc<Id>(2 * (cap ? cap : 1));  // every pair gives an entry of the window
+  if (!ws.ok()) return ST_CUDA;
+  if (cudaMemcpyAsync(dlist, list.data(), L * 8, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return ST_CUDA;
+  {
+    ProfScope ps(PROF_OTHER, s);
+    gather_counts<<<grid_for(L, 256, 152 * 8), 256, 0, s>>>(d_counts, dlist, L, cnt);
+    if (launch_ok()) return ST_CUDA;
+  }
+  if ((st = scan_exclusive_u64(cnt, off, L, ws, s))) return st;
+  const RowBounds rb = RowBounds::make(up.n, P);
+  UndListGeom g{UndGeom{up.n, P, rb}, dlist};
+  if ((st = run_chunks(g, 0, L, cnt, up.d, K_MAX, seed, int(sizeof(Id)), pairs, cap, ws, s, err)))
+    return st;
+  {
+    ProfScope ps(PROF_OTHER, s);
+    clamp_count<<<1, 1, 0, s>>>(off + L, cap, npairs);
+    if (launch_ok()) return ST_CUDA;
+  }
+  const uint64_t row_lo = rb(b0), nrows = rb(b1) - row_lo;
+  uint64_t* rowptr = nullptr;
+  Id* out = static_cast<Id*>(d_out);
+  if ((st = assemble<Id>(pairs, npairs, 0, up.n, out, cap, ws, s, err, row_lo, nrows, &rowptr,
+                         cap)))
+    return st;
+  if (d_entries && cudaMemcpyAsync(d_entries, rowptr + nrows, 8, cudaMemcpyDeviceToDevice, s) !=
+                       cudaSuccess)
+    return ST_CUDA;
+  if (d_digest || d_hist) {
+    const uint64_t nb = b1 - b0;
+    if ((d_digest && cudaMemsetAsync(d_digest, 0, nb * 8, s) != cudaSuccess) ||
+        (d_hist && cudaMemsetAsync(d_hist, 0, nb * 65 * 8, s) != cudaSuccess))
+      return ST_CUDA;
+    ProfScope ps(PROF_DIGEST, s);
+    und_block_digest<Id><<<grid_for(nrows, 256, 152 * 16), 256, 0, s>>>(
+        out, rowptr, row_lo, nrows, rb, b0, reinterpret_cast<unsigned long long*>(d_digest),
+        reinterpret_cast<unsigned long long*>(d_hist));
+    if (launch_ok()) return ST_CUDA;
+  }
+  return ST_OK;
 }
 
 // ---------------------------------------------------------------- G(n,p)
@@ -270,6 +376,41 @@ kg_status kg_gnm_undirected_ex(uint64_t n, uint64_t m, uint64_t seed, uint32_t c
   cudaStream_t s = as_stream(stream);
   st = id_bytes == 4 ? gnm_undirected_impl<uint32_t>(up, seed, k_max, d_out, cap_edges, s, err)
                      : gnm_undirected_impl<uint64_t>(up, seed, k_max, d_out, cap_edges, s, err);
+  return kg_status(st);
+}
+
+kg_status kg_gnm_undirected_chunk_counts(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                                         uint64_t* d_counts, void* stream) {
+  UndParams up;
+  int st = check_undirected(n, m, chunks, K_LEAF, K_MAX, 8, up, true);
+  if (st) return kg_status(st);
+  if (!d_counts) return KG_ERR_ARG;
+  int* err = device_error_word();
+  if (!err) return KG_ERR_CUDA;
+  cudaStream_t s = as_stream(stream);
+  Workspace ws(s);
+  return kg_status(run_quadtree(up, seed, d_counts, ws, s, err));
+}
+
+kg_status kg_gnm_undirected_rows(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
+                                 uint32_t b_begin, uint32_t b_end, const uint64_t* d_counts,
+                                 int id_bytes, void* d_out, uint64_t cap_edges, uint64_t* d_entries,
+                                 uint64_t* d_block_digest, uint64_t* d_block_hist, void* stream) {
+  UndParams up;
+  int st = check_undirected(n, m, chunks, K_LEAF, K_MAX, id_bytes, up, true);
+  if (st) return kg_status(st);
+  if (b_begin >= b_end || b_end > chunks) return KG_ERR_ARG;
+  if (!d_out && cap_edges > 0) return KG_ERR_ARG;
+  int* err = device_error_word();
+  if (!err) return KG_ERR_CUDA;
+  cudaStream_t s = as_stream(stream);
+  st = id_bytes == 4
+           ? gnm_undirected_rows_impl<uint32_t>(up, seed, b_begin, b_end, d_counts, d_out,
+                                                cap_edges, d_entries, d_block_digest, d_block_hist,
+                                                s, err)
+           : gnm_undirected_rows_impl<uint64_t>(up, seed, b_begin, b_end, d_counts, d_out,
+                                                cap_edges, d_entries, d_block_digest, d_block_hist,
+                                                s, err);
   return kg_status(st);
 }
 

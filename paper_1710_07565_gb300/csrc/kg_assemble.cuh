@@ -7,40 +7,47 @@
 
 namespace kg {
 
-// pairs (u > v) -> both directions, sorted by (u, v), into out[0 .. 2 npairs)
+// pairs (u > v) -> both directions, sorted by (u, v), into out[0 ..): the
+// rows [row_lo, row_lo + nrows) (all n rows by default).  rowptr_out, when
+// given, receives the nrows + 1 row offsets (device); its last entry is the
+// number of entries written.
 template <class Id>
 inline int assemble(const Id* pairs, const uint64_t* npairs_dev, uint64_t npairs_host, uint64_t n,
-                    Id* out, uint64_t cap, Workspace& ws, cudaStream_t s, int* err) {
-  unsigned long long* deg = ws.alloc<unsigned long long>(n);
-  uint64_t* rowptr = ws.alloc<uint64_t>(n + 1);
-  unsigned long long* cursor = ws.alloc<unsigned long long>(n);
-  unsigned long long* long_rows = ws.alloc<unsigned long long>(n);
+                    Id* out, uint64_t cap, Workspace& ws, cudaStream_t s, int* err,
+                    uint64_t row_lo = 0, uint64_t nrows = ~uint64_t(0),
+                    uint64_t** rowptr_out = nullptr, uint64_t work_bound = 0) {
+  if (nrows == ~uint64_t(0)) nrows = n;
+  unsigned long long* deg = ws.alloc<unsigned long long>(nrows);
+  uint64_t* rowptr = ws.alloc<uint64_t>(nrows + 1);
+  unsigned long long* cursor = ws.alloc<unsigned long long>(nrows);
+  unsigned long long* long_rows = ws.alloc<unsigned long long>(nrows);
   unsigned long long* nlong = ws.alloc<unsigned long long>(1);
   if (!ws.ok()) return ST_CUDA;
-  if (cudaMemsetAsync(deg, 0, n * 8, s) != cudaSuccess ||
+  if (rowptr_out) *rowptr_out = rowptr;
+  if (cudaMemsetAsync(deg, 0, nrows * 8, s) != cudaSuccess ||
       cudaMemsetAsync(nlong, 0, 8, s) != cudaSuccess)
     return ST_CUDA;
-  const uint64_t work = npairs_dev ? cap / 2 : npairs_host;
+  const uint64_t work = work_bound ? work_bound : (npairs_dev ? cap / 2 : npairs_host);
   {
     ProfScope ps(PROF_ASSEMBLY, s);
     und_degree<Id><<<grid_for(work, 256, 152 * 16), 256, 0, s>>>(pairs, npairs_dev, npairs_host,
-                                                                 deg);
+                                                                 row_lo, nrows, deg);
     if (launch_ok()) return ST_CUDA;
   }
-  int st = scan_exclusive_u64(reinterpret_cast<const uint64_t*>(deg), rowptr, n, ws, s);
+  int st = scan_exclusive_u64(reinterpret_cast<const uint64_t*>(deg), rowptr, nrows, ws, s);
   if (st) return st;
-  if (cudaMemcpyAsync(cursor, rowptr, n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+  if (cudaMemcpyAsync(cursor, rowptr, nrows * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
     return ST_CUDA;
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    und_scatter<Id><<<grid_for(work, 256, 152 * 16), 256, 0, s>>>(pairs, npairs_dev, npairs_host,
-                                                                  cursor, out, cap, err);
+    und_scatter<Id><<<grid_for(work, 256, 152 * 16), 256, 0, s>>>(
+        pairs, npairs_dev, npairs_host, row_lo, nrows, cursor, out, cap, err);
     if (launch_ok()) return ST_CUDA;
   }
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    und_sort_short<Id><<<grid_for(n, 8, 152 * 32), 256, 0, s>>>(rowptr, n, out, cap, long_rows,
-                                                                nlong);
+    und_sort_short<Id><<<grid_for(nrows, 8, 152 * 32), 256, 0, s>>>(rowptr, nrows, out, cap,
+                                                                    long_rows, nlong);
     if (launch_ok()) return ST_CUDA;
   }
   ProfScope ps(PROF_ASSEMBLY, s);

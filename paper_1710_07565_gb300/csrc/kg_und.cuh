@@ -141,40 +141,74 @@ __device__ __forceinline__ void store_pair(Id* out, uint64_t i, uint64_t u, uint
     reinterpret_cast<ulonglong2*>(out)[i] = make_ulonglong2(u, v);
 }
 
+// Rows [row_lo, row_lo + nrows) only: a pair (u, v) gives the entry (u, v)
+// when u is in the window and (v, u) when v is (all rows: row_lo 0, nrows n).
 template <class Id>
 __global__ void und_degree(const Id* __restrict__ pairs, const uint64_t* __restrict__ npairs_dev,
-                           uint64_t npairs_host, unsigned long long* __restrict__ deg) {
+                           uint64_t npairs_host, uint64_t row_lo, uint64_t nrows,
+                           unsigned long long* __restrict__ deg) {
   const uint64_t np = npairs_dev ? *npairs_dev : npairs_host;
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np;
        i += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t u, v;
     load_pair(pairs, i, u, v);
-    atomicAdd(&deg[u], 1ull);
-    atomicAdd(&deg[v], 1ull);
+    if (u - row_lo < nrows) atomicAdd(&deg[u - row_lo], 1ull);
+    if (v - row_lo < nrows) atomicAdd(&deg[v - row_lo], 1ull);
   }
 }
 
 template <class Id>
 __global__ void und_scatter(const Id* __restrict__ pairs, const uint64_t* __restrict__ npairs_dev,
-                            uint64_t npairs_host, unsigned long long* __restrict__ cursor,
-                            Id* __restrict__ out, uint64_t cap, int* err) {
+                            uint64_t npairs_host, uint64_t row_lo, uint64_t nrows,
+                            unsigned long long* __restrict__ cursor, Id* __restrict__ out,
+                            uint64_t cap, int* err) {
   const uint64_t np = npairs_dev ? *npairs_dev : npairs_host;
   for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < np;
        i += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t u, v;
     load_pair(pairs, i, u, v);
-    const uint64_t p = atomicAdd(&cursor[u], 1ull);
-    const uint64_t q = atomicAdd(&cursor[v], 1ull);
-    if (p < cap) {
-      store_pair(out, p, u, v);
-    } else {
-      set_error(err, ST_CAPACITY);
+    if (u - row_lo < nrows) {
+      const uint64_t p = atomicAdd(&cursor[u - row_lo], 1ull);
+      if (p < cap)
+        store_pair(out, p, u, v);
+      else
+        set_error(err, ST_CAPACITY);
     }
-    if (q < cap) {
-      store_pair(out, q, v, u);
-    } else {
-      set_error(err, ST_CAPACITY);
+    if (v - row_lo < nrows) {
+      const uint64_t q = atomicAdd(&cursor[v - row_lo], 1ull);
+      if (q < cap)
+        store_pair(out, q, v, u);
+      else
+        set_error(err, ST_CAPACITY);
     }
+  }
+}
+
+// Per row block of the window: the digest of its entries and the histogram
+// of its rows' degrees (rows [r_b, r_{b+1}) of block b_lo + (index)).
+template <class Id>
+__global__ void und_block_digest(const Id* __restrict__ out, const uint64_t* __restrict__ rowptr,
+                                 uint64_t row_lo, uint64_t nrows, RowBounds rb, uint32_t b_lo,
+                                 unsigned long long* __restrict__ digest,
+                                 unsigned long long* __restrict__ hist) {
+  for (uint64_t r = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < nrows;
+       r += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t u = row_lo + r;
+    // block of row u: rb(b) <= u < rb(b + 1)
+    uint64_t b = uint64_t((u128(u) * rb.P) / rb.n);
+    while (b + 1 < rb.P && rb(b + 1) <= u) ++b;
+    while (b > 0 && rb(b) > u) --b;
+    const uint64_t e0 = rowptr[r], e1 = rowptr[r + 1];
+    const uint64_t deg = e1 - e0;
+    unsigned long long dsum = 0;
+    for (uint64_t e = e0; e < e1; ++e) {
+      uint64_t a, c;
+      load_pair(out, e, a, c);
+      dsum += edge_hash(a, c);
+    }
+    const uint64_t bi = b - b_lo;
+    if (digest && dsum) atomicAdd(&digest[bi], dsum);
+    if (hist) atomicAdd(&hist[bi * 65 + (deg < 64 ? deg : 64)], 1ull);
   }
 }
 

@@ -155,3 +155,68 @@ def test_gnp_binomial_zero_capacity_and_range(kg):
     # chunks of 2^66 pairs are beyond the binomial's exact range
     assert L.kg_gnp_binomial(0, 1 << 40, 1e-9, 1, 16, 8, out.data_ptr(), 16, cnt.data_ptr(), s) \
         == kg.KG_ERR_RANGE
+
+
+# ---------------------------------------------------------------- undirected rows by row blocks
+
+def _rows(kg, n, m, seed, P, b0, b1, id_bytes, cap, counts=None):
+    import torch
+    s = kg._stream_ptr(None)
+    out = torch.zeros((max(cap, 1), 2), dtype=torch.int64 if id_bytes == 8 else torch.int32,
+                      device="cuda")
+    ent = torch.zeros(1, dtype=torch.int64, device="cuda")
+    dig = torch.zeros(b1 - b0, dtype=torch.int64, device="cuda")
+    hist = torch.zeros((b1 - b0, 65), dtype=torch.int64, device="cuda")
+    kg.kg_gnm_undirected_rows(n, m, seed, P, b0, b1, counts.data_ptr() if counts is not None else 0,
+                              id_bytes, out.data_ptr(), cap, ent.data_ptr(), dig.data_ptr(),
+                              hist.data_ptr(), s)
+    kg.check_device_error()
+    k = int(ent.item())
+    return (out[:k], dig.cpu().numpy().view(np.uint64), hist.cpu().numpy().view(np.uint64))
+
+
+@pytest.mark.parametrize("n,m,seed,P,ranges,id_bytes", [
+    (1000, 20000, 3, 7, [(0, 1), (1, 4), (4, 7)], 4),
+    (5000, 5000 * 4999 // 4, 4, 4, [(1, 3)], 4),            # rows of ~2500 entries
+    (333, 1000, 5, 333, [(0, 100), (100, 101), (101, 333)], 8),
+    ((1 << 20) + 7, 1 << 22, 6, 32, [(5, 9), (31, 32)], 8),
+])
+def test_undirected_rows_bit_exact(kg, orc, n, m, seed, P, ranges, id_bytes):
+    """Rows of a range of row blocks: equal to the oracle's rows, digest and
+    degree histogram of every block equal to the oracle's."""
+    for b0, b1 in ranges:
+        ou, ov = orc.gnm_undirected_rows(n, m, seed, P, b0, b1)
+        t, dig, hist = _rows(kg, n, m, seed, P, b0, b1, id_bytes, len(ou) + 16)
+        gu, gv = edges_np(t, id_bytes)
+        assert_same_edges(gu, gv, ou, ov, f"rows n={n} blocks [{b0},{b1})")
+        for b in range(b0, b1):
+            lo, hi = b * n // P, (b + 1) * n // P
+            sel = (ou >= lo) & (ou < hi)
+            assert int(dig[b - b0]) == orc.edge_checksum(ou[sel], ov[sel])
+            assert np.array_equal(hist[b - b0], orc.outdegree_hist(ou[sel], lo, hi))
+
+
+def test_undirected_rows_concatenate_to_the_whole_graph(kg):
+    import torch
+    n, m, P, seed = 30000, 400000, 9, 7
+    whole = kg.gnm_undirected(n, m, seed, P).clone()
+    parts = [_rows(kg, n, m, seed, P, b0, b1, 4, 2 * m)[0] for b0, b1 in [(0, 2), (2, 3), (3, 9)]]
+    assert torch.equal(torch.cat(parts), whole)
+
+
+def test_undirected_rows_at_scale_sampled_blocks(kg, orc):
+    """n = 2^32 vertices (uint64 ids), m = 2^31, 1024 x 1024 chunk matrix: two
+    sampled row blocks against the oracle (chunk counts drawn once on the GPU)."""
+    import torch
+    n, m, P, seed = 1 << 32, 1 << 31, 1024, 1
+    counts = torch.zeros(P * (P + 1) // 2, dtype=torch.int64, device="cuda")
+    kg.kg_gnm_undirected_chunk_counts(n, m, seed, P, counts.data_ptr(), kg._stream_ptr(None))
+    assert int(counts.sum()) == m
+    for b in (3, 700):
+        ou, ov = orc.gnm_undirected_rows(n, m, seed, P, b, b + 1, cap_hint=1 << 24)
+        t, dig, hist = _rows(kg, n, m, seed, P, b, b + 1, 8, len(ou) + 16, counts)
+        gu, gv = edges_np(t, 8)
+        assert_same_edges(gu, gv, ou, ov, f"block {b}")
+        lo, hi = b * n // P, (b + 1) * n // P
+        assert int(dig[0]) == orc.edge_checksum(ou, ov)
+        assert np.array_equal(hist[0], orc.outdegree_hist(ou, lo, hi))
