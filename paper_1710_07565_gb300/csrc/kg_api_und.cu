@@ -1,5 +1,6 @@
 // C ABI: undirected G(n,m) (Sec. 4.2) and G(n,p) (Sec. 4.3), directed and
 // undirected, with the assembly of undirected output in both directions.
+#include <algorithm>
 #include <vector>
 
 #include "kg.h"
@@ -88,7 +89,8 @@ static int gnm_undirected_impl(const UndParams& up, uint64_t seed, uint32_t k_ma
 // ---------------------------------------------------------------- undirected rows by blocks
 // The chunks (i, j <= i) a range of row blocks needs (Sec. 4.2: a PE
 // regenerates the chunks of its row and of its column), given as a device
-// list of chunk indices k = i(i+1)/2 + j in increasing order.
+// list of chunk indices k = i(i+1)/2 + j (the row blocks' chunks, then the
+// column blocks' chunks outside them).
 struct UndListGeom {
   UndGeom base;
   const uint64_t* list;
@@ -133,10 +135,14 @@ static int gnm_undirected_rows_impl(const UndParams& up, uint64_t seed, uint32_t
     if ((st = run_quadtree(up, seed, c2, ws, s, err))) return st;
     d_counts = c2;
   }
+  // chunks (i, j <= i) of the row blocks, then (i > j, j) of the column blocks
+  // whose row block lies outside the range (those inside are already listed)
   std::vector<uint64_t> list;
-  for (uint64_t i = 0; i < P; ++i)
-    for (uint64_t j = 0; j <= i; ++j)
-      if ((i >= b0 && i < b1) || (j >= b0 && j < b1)) list.push_back(i * (i + 1) / 2 + j);
+  for (uint64_t i = b0; i < b1; ++i)
+    for (uint64_t j = 0; j <= i; ++j) list.push_back(i * (i + 1) / 2 + j);
+  for (uint64_t j = b0; j < b1; ++j)
+    for (uint64_t i = std::max<uint64_t>(j + 1, b1); i < P; ++i)
+      list.push_back(i * (i + 1) / 2 + j);
   const uint64_t L = list.size();
   uint64_t* dlist = ws.alloc<uint64_t>(L);
   uint64_t* cnt = ws.alloc<uint64_t>(L);

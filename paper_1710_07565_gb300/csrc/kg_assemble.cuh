@@ -46,7 +46,7 @@ inline int assemble(const Id* pairs, const uint64_t* npairs_dev, uint64_t npairs
   }
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    und_sort_short<Id><<<grid_for(nrows, 8, 152 * 32), 256, 0, s>>>(rowptr, nrows, out, cap,
+    und_sort_short<Id><<<grid_for(nrows, 256, 152 * 32), 256, 0, s>>>(rowptr, nrows, out, cap,
                                                                     long_rows, nlong);
     if (launch_ok()) return ST_CUDA;
   }

@@ -404,7 +404,7 @@ __global__ void batch_und_scatter(const BInst* __restrict__ inst, uint32_t count
   }
 }
 
-// Rows of <= WARP_SORT_MAX entries sorted by one warp; longer rows listed.
+// Rows of <= WARP_SORT_MAX entries sorted by their lane or their warp; longer rows listed.
 __global__ void __launch_bounds__(256)
     batch_und_sort_short(uint64_t nverts, const unsigned long long* __restrict__ rowpos,
                          const unsigned long long* __restrict__ deg, uint32_t* __restrict__ out,
@@ -412,14 +412,15 @@ __global__ void __launch_bounds__(256)
   const unsigned lane = threadIdx.x & 31;
   const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  for (uint64_t r = warp; r < nverts; r += nwarps) {
-    const uint64_t b = rowpos[r], dg = deg[r];
-    if (dg <= 1 || b + dg > cap) continue;
-    if (dg > WARP_SORT_MAX) {
-      if (lane == 0) long_rows[atomicAdd(nlong, 1ull)] = r;
-      continue;
+  for (uint64_t r0 = warp * 32; r0 < nverts; r0 += nwarps * 32) {  // uniform over the warp
+    const uint64_t r = r0 + lane;
+    uint64_t b = 0, dg = 0;
+    if (r < nverts) {
+      b = rowpos[r];
+      dg = deg[r];
+      if (b + dg > cap) dg = 0;
     }
-    warp_sort_row(out, b, dg, lane);
+    sort_rows_of_warp(out, b, dg, r, lane, long_rows, nlong);
   }
 }
 
@@ -604,7 +605,7 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
   }
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    batch_und_sort_short<<<grid_for(V, 8, 152 * 32), 256, 0, s>>>(V, bp->rowpos, bp->deg, out, cap,
+    batch_und_sort_short<<<grid_for(V, 256, 152 * 32), 256, 0, s>>>(V, bp->rowpos, bp->deg, out, cap,
                                                                   bp->long_rows, bp->nlong);
     if (launch_ok()) return ST_CUDA;
   }

@@ -279,8 +279,53 @@ __device__ __forceinline__ void warp_sort_row(Id* out, uint64_t b, uint64_t deg,
     warp_sort_row_e<8>(out, b, deg, lane);
 }
 
-// Rows of at most WARP_SORT_MAX entries: one warp per row.  Longer rows are
-// listed for und_sort_long.
+constexpr uint64_t LANE_SORT_MAX = 8;
+
+// Sorts the second ids of row entries [b, b + deg), deg <= 8, by one thread:
+// an 8-input sorting network (19 comparators) over registers padded with +inf.
+template <class Id>
+__device__ __forceinline__ void lane_sort_row(Id* out, uint64_t b, uint64_t deg) {
+  uint64_t x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = uint64_t(i) < deg ? uint64_t(out[2 * (b + i) + 1]) : ~uint64_t(0);
+  auto cx = [&](int i, int j) {
+    const uint64_t a = x[i] < x[j] ? x[i] : x[j], c = x[i] < x[j] ? x[j] : x[i];
+    x[i] = a;
+    x[j] = c;
+  };
+  cx(0, 2); cx(1, 3); cx(4, 6); cx(5, 7);
+  cx(0, 4); cx(1, 5); cx(2, 6); cx(3, 7);
+  cx(0, 1); cx(2, 3); cx(4, 5); cx(6, 7);
+  cx(2, 4); cx(3, 5);
+  cx(1, 4); cx(3, 6);
+  cx(1, 2); cx(3, 4); cx(5, 6);
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    if (uint64_t(i) < deg) out[2 * (b + i) + 1] = Id(x[i]);
+}
+
+// Rows of one warp's 32 consecutive rows: those of at most LANE_SORT_MAX
+// entries by their own lane, those up to WARP_SORT_MAX by the whole warp one
+// after the other, longer ones listed for und_sort_long.  Every lane of the
+// warp calls it (b, deg: this lane's row; u: its row index).
+template <class Id>
+__device__ __forceinline__ void sort_rows_of_warp(Id* out, uint64_t b, uint64_t deg, uint64_t u,
+                                                  unsigned lane, unsigned long long* long_rows,
+                                                  unsigned long long* nlong) {
+  if (deg >= 2 && deg <= LANE_SORT_MAX) lane_sort_row(out, b, deg);
+  unsigned m = __ballot_sync(0xffffffffu, deg > LANE_SORT_MAX);
+  while (m) {
+    const int l = __ffs(m) - 1;
+    m &= m - 1;
+    const uint64_t bl = __shfl_sync(0xffffffffu, b, l), dl = __shfl_sync(0xffffffffu, deg, l);
+    if (dl > WARP_SORT_MAX) {
+      if (lane == unsigned(l)) long_rows[atomicAdd(nlong, 1ull)] = u;
+    } else {
+      warp_sort_row(out, bl, dl, lane);
+    }
+  }
+}
+
 template <class Id>
 __global__ void __launch_bounds__(256)
     und_sort_short(const uint64_t* __restrict__ rowptr, uint64_t n, Id* __restrict__ out,
@@ -288,15 +333,15 @@ __global__ void __launch_bounds__(256)
   const unsigned lane = threadIdx.x & 31;
   const uint64_t warp = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  for (uint64_t u = warp; u < n; u += nwarps) {
-    const uint64_t b = rowptr[u], e = rowptr[u + 1] < cap ? rowptr[u + 1] : cap;
-    if (e <= b + 1) continue;
-    const uint64_t deg = e - b;
-    if (deg > WARP_SORT_MAX) {
-      if (lane == 0) long_rows[atomicAdd(nlong, 1ull)] = u;
-      continue;
+  for (uint64_t u0 = warp * 32; u0 < n; u0 += nwarps * 32) {  // uniform over the warp
+    const uint64_t u = u0 + lane;
+    uint64_t b = 0, deg = 0;
+    if (u < n) {
+      b = rowptr[u];
+      const uint64_t e = rowptr[u + 1] < cap ? rowptr[u + 1] : cap;
+      deg = e > b ? e - b : 0;
     }
-    warp_sort_row(out, b, deg, lane);
+    sort_rows_of_warp(out, b, deg, u, lane, long_rows, nlong);
   }
 }
 
