@@ -203,13 +203,14 @@ def _timed(fn, reps, warm=2):
     return statistics.median(ts)
 
 
-def undirected_at_scale(kg, reps=2):
+def undirected_at_scale(kg, reps=2, ranges=256):
     import torch
-    n, m, P, seed, ranges = 1 << 32, 1 << 32, 4096, 1, 16
+    n, m, P, seed = 1 << 32, 1 << 32, 4096, 1
     per = P // ranges
     s = torch.cuda.current_stream().cuda_stream
     counts = torch.zeros(P * (P + 1) // 2, dtype=torch.int64, device="cuda")
-    cap = (1 << 29) + (1 << 22)  # entries of one range: mean 2^29
+    mean = (2 * m) // ranges  # entries of one range
+    cap = mean + 64 * int(mean ** 0.5) + 4096
     out = torch.empty((cap, 2), dtype=torch.int64, device="cuda")
     ent = torch.zeros(ranges, dtype=torch.int64, device="cuda")
     dig = torch.zeros(P, dtype=torch.int64, device="cuda")
@@ -270,8 +271,8 @@ def other_workloads(kg, serve_requests=1000):
     del out, cnt
     kg.check_device_error()
     # undirected G(n,m) at scale by row blocks (Sec. 4.2): n = 2^32, m = 2^32
-    # (2^33 entries, uint64 ids, 128 GiB), 4096 x 4096 chunk matrix, 16 ranges of
-    # 256 row blocks, each with per-block digests and degree histograms
+    # (2^33 entries, uint64 ids, 128 GiB), 4096 x 4096 chunk matrix, 256 ranges of
+    # 16 row blocks, each with per-block digests and degree histograms
     res["gnm_undirected_n2e32_m2e32_P4096_rows"] = undirected_at_scale(kg)
     torch.cuda.empty_cache()
     # batched: 4096 instances, one launch sequence (CUDA graph) vs 4096 separate calls

@@ -182,7 +182,7 @@ static int gnm_undirected_rows_impl(const UndParams& up, uint64_t seed, uint32_t
         (d_hist && cudaMemsetAsync(d_hist, 0, nb * 65 * 8, s) != cudaSuccess))
       return ST_CUDA;
     ProfScope ps(PROF_DIGEST, s);
-    und_block_digest<Id><<<grid_for(nrows, 256, 152 * 16), 256, 0, s>>>(
+    und_block_digest<Id><<<grid_for(nrows, unsigned(DIGEST_SEG), 152 * 16), 256, 0, s>>>(
         out, rowptr, row_lo, nrows, rb, b0, reinterpret_cast<unsigned long long*>(d_digest),
         reinterpret_cast<unsigned long long*>(d_hist));
     if (launch_ok()) return ST_CUDA;

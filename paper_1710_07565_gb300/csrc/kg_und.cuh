@@ -185,30 +185,74 @@ __global__ void und_scatter(const Id* __restrict__ pairs, const uint64_t* __rest
 }
 
 // Per row block of the window: the digest of its entries and the histogram
-// of its rows' degrees (rows [r_b, r_{b+1}) of block b_lo + (index)).
+// of its rows' degrees (rows [r_b, r_{b+1}) of block b_lo + (index)).  A CTA
+// takes segments of 8192 consecutive rows (almost always inside one row
+// block, 2^20 rows wide at scale): degrees 0..7 are counted in registers and
+// summed over the warp, the rest and the digest in shared memory, and the
+// segment's block receives one atomic per bin; rows of a second block in a
+// segment go to global memory directly.
+constexpr uint64_t DIGEST_SEG = 8192;
+
+__device__ __forceinline__ uint64_t block_of_row(const RowBounds& rb, uint64_t u) {
+  uint64_t b = uint64_t((u128(u) * rb.P) / rb.n);
+  while (b + 1 < rb.P && rb(b + 1) <= u) ++b;
+  while (b > 0 && rb(b) > u) --b;
+  return b;
+}
+
 template <class Id>
-__global__ void und_block_digest(const Id* __restrict__ out, const uint64_t* __restrict__ rowptr,
-                                 uint64_t row_lo, uint64_t nrows, RowBounds rb, uint32_t b_lo,
-                                 unsigned long long* __restrict__ digest,
-                                 unsigned long long* __restrict__ hist) {
-  for (uint64_t r = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < nrows;
-       r += uint64_t(gridDim.x) * blockDim.x) {
-    const uint64_t u = row_lo + r;
-    // block of row u: rb(b) <= u < rb(b + 1)
-    uint64_t b = uint64_t((u128(u) * rb.P) / rb.n);
-    while (b + 1 < rb.P && rb(b + 1) <= u) ++b;
-    while (b > 0 && rb(b) > u) --b;
-    const uint64_t e0 = rowptr[r], e1 = rowptr[r + 1];
-    const uint64_t deg = e1 - e0;
+__global__ void __launch_bounds__(256)
+    und_block_digest(const Id* __restrict__ out, const uint64_t* __restrict__ rowptr,
+                     uint64_t row_lo, uint64_t nrows, RowBounds rb, uint32_t b_lo,
+                     unsigned long long* __restrict__ digest,
+                     unsigned long long* __restrict__ hist) {
+  __shared__ unsigned long long sh_hist[65];
+  __shared__ unsigned long long sh_dig;
+  const unsigned lane = threadIdx.x & 31;
+  for (uint64_t s0 = uint64_t(blockIdx.x) * DIGEST_SEG; s0 < nrows;
+       s0 += uint64_t(gridDim.x) * DIGEST_SEG) {
+    const uint64_t s1 = s0 + DIGEST_SEG < nrows ? s0 + DIGEST_SEG : nrows;
+    const uint64_t bA = block_of_row(rb, row_lo + s0);
+    const bool one = block_of_row(rb, row_lo + s1 - 1) == bA;
+    for (int i = threadIdx.x; i < 65; i += blockDim.x) sh_hist[i] = 0;
+    if (threadIdx.x == 0) sh_dig = 0;
+    __syncthreads();
+    uint32_t c[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     unsigned long long dsum = 0;
-    for (uint64_t e = e0; e < e1; ++e) {
-      uint64_t a, c;
-      load_pair(out, e, a, c);
-      dsum += edge_hash(a, c);
+    for (uint64_t r = s0 + threadIdx.x; r < s1; r += blockDim.x) {
+      const uint64_t e0 = rowptr[r], e1 = rowptr[r + 1];
+      const uint64_t deg = e1 - e0;
+      unsigned long long ds = 0;
+      for (uint64_t e = e0; e < e1; ++e) {
+        uint64_t a, b2;
+        load_pair(out, e, a, b2);
+        ds += edge_hash(a, b2);
+      }
+      if (one || block_of_row(rb, row_lo + r) == bA) {
+        dsum += ds;
+#pragma unroll
+        for (int d = 0; d < 8; ++d) c[d] += (deg == uint64_t(d));
+        if (deg >= 8) atomicAdd(&sh_hist[deg < 64 ? deg : 64], 1ull);
+      } else {  // the segment's second block
+        const uint64_t bi = block_of_row(rb, row_lo + r) - b_lo;
+        if (digest && ds) atomicAdd(&digest[bi], ds);
+        if (hist) atomicAdd(&hist[bi * 65 + (deg < 64 ? deg : 64)], 1ull);
+      }
     }
-    const uint64_t bi = b - b_lo;
-    if (digest && dsum) atomicAdd(&digest[bi], dsum);
-    if (hist) atomicAdd(&hist[bi * 65 + (deg < 64 ? deg : 64)], 1ull);
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      const unsigned t = __reduce_add_sync(0xffffffffu, c[d]);
+      if (lane == 0 && t) atomicAdd(&sh_hist[d], (unsigned long long)t);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+    if (lane == 0 && dsum) atomicAdd(&sh_dig, dsum);
+    __syncthreads();
+    const uint64_t bi = bA - b_lo;
+    for (int i = threadIdx.x; i < 65; i += blockDim.x)
+      if (hist && sh_hist[i]) atomicAdd(&hist[bi * 65 + i], sh_hist[i]);
+    if (threadIdx.x == 0 && digest && sh_dig) atomicAdd(&digest[bi], sh_dig);
+    __syncthreads();
   }
 }
 
