@@ -62,14 +62,7 @@ static int check_directed(uint64_t n, uint64_t m, uint32_t P, uint32_t k_leaf, u
   return ST_OK;
 }
 
-static DirGeom dir_geom(uint64_t n, uint32_t P) {
-  DirGeom g;
-  g.n = n;
-  g.P = P;
-  g.div = make_div(n > 1 ? n - 1 : 1);
-  g.rb = RowBounds::make(n, P);
-  return g;
-}
+static DirGeom dir_geom(uint64_t n, uint32_t P) { return DirGeom::make(n, P); }
 
 // Chunk split tree: bands of 8 levels, one block per subtree root.
 static int run_chunk_tree(const DirParams& dp, uint64_t seed, uint64_t* cnt, Workspace& ws,

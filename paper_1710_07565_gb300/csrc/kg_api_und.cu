@@ -336,11 +336,7 @@ static int gnpb_impl(int undirected, uint64_t n, double p, uint64_t seed, uint32
   const uint64_t mult = undirected ? 2 : 1;
   int st;
   if (!undirected) {
-    DirGeom g;
-    g.n = n;
-    g.P = P;
-    g.div = make_div(n - 1);
-    g.rb = RowBounds::make(n, P);
+    const DirGeom g = DirGeom::make(n, P);
     if ((st = gnpb_counts(g, C, p, seed, cnt, s, err))) return st;
     if ((st = scan_exclusive_u64(cnt, off, C, ws, s))) return st;
     {
@@ -482,11 +478,7 @@ kg_status kg_gnp_ex(int undirected, uint64_t n, double p, uint64_t seed, uint32_
              ? gnp_dispatch_slots<UndGeom, uint32_t>(g, C, true, n, pl, seed, d_out, cap_edges, d_count, s, err)
              : gnp_dispatch_slots<UndGeom, uint64_t>(g, C, true, n, pl, seed, d_out, cap_edges, d_count, s, err);
   } else {
-    DirGeom g;
-    g.n = n;
-    g.P = chunks;
-    g.div = make_div(n - 1);
-    g.rb = RowBounds::make(n, chunks);
+    const DirGeom g = DirGeom::make(n, chunks);
     st = id_bytes == 4
              ? gnp_dispatch_slots<DirGeom, uint32_t>(g, C, false, n, pl, seed, d_out, cap_edges, d_count, s, err)
              : gnp_dispatch_slots<DirGeom, uint64_t>(g, C, false, n, pl, seed, d_out, cap_edges, d_count, s, err);
@@ -510,11 +502,7 @@ kg_status kg_gnp_count(int undirected, uint64_t n, double p, uint64_t seed, uint
     UndGeom g{n, chunks, RowBounds::make(n, chunks)};
     st = gnp_count_impl(g, C, true, pl, seed, d_count, s, err);
   } else {
-    DirGeom g;
-    g.n = n;
-    g.P = chunks;
-    g.div = make_div(n - 1);
-    g.rb = RowBounds::make(n, chunks);
+    const DirGeom g = DirGeom::make(n, chunks);
     st = gnp_count_impl(g, C, false, pl, seed, d_count, s, err);
   }
   return kg_status(st);
@@ -561,11 +549,7 @@ kg_status kg_gnp_binomial_count(int undirected, uint64_t n, double p, uint64_t s
     UndGeom g{n, chunks, RowBounds::make(n, chunks)};
     st = gnpb_counts(g, C, p, seed, cnt, s, err);
   } else {
-    DirGeom g;
-    g.n = n;
-    g.P = chunks;
-    g.div = make_div(n - 1);
-    g.rb = RowBounds::make(n, chunks);
+    const DirGeom g = DirGeom::make(n, chunks);
     st = gnpb_counts(g, C, p, seed, cnt, s, err);
   }
   if (st) return kg_status(st);

@@ -53,6 +53,15 @@ struct DirGeom {
   DivU64 div;  // division by n-1
   RowBounds rb;
 
+  static DirGeom make(uint64_t n, uint32_t P) {
+    DirGeom g;
+    g.n = n;
+    g.P = P;
+    g.div = make_div(n > 1 ? n - 1 : 1);
+    g.rb = RowBounds::make(n, P);
+    return g;
+  }
+
   __host__ __device__ __forceinline__ uint64_t chunk_id(uint64_t c) const { return c; }
   __host__ __device__ __forceinline__ uint64_t rows(uint64_t c) const { return rb(c + 1) - rb(c); }
   __host__ __device__ __forceinline__ uint64_t universe(uint64_t c) const {
