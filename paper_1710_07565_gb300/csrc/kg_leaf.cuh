@@ -508,13 +508,11 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
         sink.put(base + r, u, v);
       }
     } else {
-      for (uint32_t r0 = 0; r0 < k; r0 += FAST_THREADS) {  // uniform over the block
-        const uint32_t r = r0 + tid;
-        const bool in = r < k;
-        const uint64_t x = in ? res[r] : 0;
-        const uint64_t xp = (in && r > 0) ? res[r - 1] : 0;  // the neighbours' offsets
-        const uint64_t xn = (r + 1 < k) ? res[r + 1] : 0;
-        if (in) {
+      for (uint32_t r = tid; r < k; r += FAST_THREADS) {
+        const uint64_t x = res[r];
+        const uint64_t xp = r > 0 ? res[r - 1] : 0;  // the neighbours' offsets
+        const uint64_t xn = r + 1 < k ? res[r + 1] : 0;
+        {
           uint64_t u, v;
           g.map(gx, lo + x, u, v);
           sink.put(base + r, u, v);
