@@ -246,6 +246,11 @@ kg_status kg_batch_destroy(kg_batch* batch);
  * without storing them. */
 kg_status kg_gnp_count(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
                        uint32_t k_leaf, uint64_t* d_count, void* stream);
+/* kg_gnp_count with the default tile parameter (k_leaf = 1024): the exact
+ * size of what kg_gnp_directed (undirected = 0) or kg_gnp_undirected
+ * (undirected = 1) writes for the same arguments. */
+kg_status kg_gnp_size(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
+                      uint64_t* d_count, void* stream);
 
 /*
  * Serving: a continuous-batching request loop (host scheduling, device work).
@@ -297,6 +302,14 @@ kg_status kg_last_error(void* stream);
 
 /* Human-readable name of a status. */
 const char* kg_status_str(kg_status s);
+
+/* Releases what the library holds on the current device: waits for the
+ * device to finish, frees the device error word (a pending error is
+ * discarded) and returns the scratch cached in the device's stream-ordered
+ * pool to the driver.  Batches and servers are owned by the caller and are
+ * not touched.  Any entry point may be called afterwards: the state is made
+ * again on first use.  Not thread-safe against concurrent calls. */
+kg_status kg_shutdown(void);
 
 /*
  * Instrumentation (no counterpart in the paper).

@@ -67,6 +67,8 @@ def lib() -> ctypes.CDLL:
                 "kg_gnp_binomial_count": [i32, u64, dbl, u64, u32, vp, vp],
                 "kg_edge_digest": [vp, u64, i32, vp, vp],
                 "kg_last_error": [vp],
+                "kg_gnp_size": [i32, u64, dbl, u64, u32, vp, vp],
+                "kg_shutdown": [],
                 "kg_gnm_directed_noalloc": [u64, u64, u64, u32, i32, vp, u64, vp, vp],
             }
             for name, args in sigs.items():
@@ -283,6 +285,14 @@ def kg_batch_destroy(h):
 
 def kg_gnp_count(undirected, n, p, seed, chunks, k_leaf, d_count, stream):
     return _call("kg_gnp_count", int(undirected), n, p, seed, chunks, k_leaf, d_count, stream)
+
+
+def kg_gnp_size(undirected, n, p, seed, chunks, d_count, stream):
+    return _call("kg_gnp_size", int(undirected), n, p, seed, chunks, d_count, stream)
+
+
+def kg_shutdown():
+    return _call("kg_shutdown")
 
 
 # request models: G(n,m); G(n,p) by geometric skips; G(n,p) by binomial chunk counts

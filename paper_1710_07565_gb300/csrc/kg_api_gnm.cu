@@ -10,9 +10,12 @@
 namespace kg {
 
 // ---------------------------------------------------------------- error word, pool
+static std::mutex g_words_mu;
+static std::unordered_map<int, int*> g_words;  // device -> error word
+
 int* device_error_word() {
-  static std::mutex mu;
-  static std::unordered_map<int, int*> words;
+  std::mutex& mu = g_words_mu;
+  std::unordered_map<int, int*>& words = g_words;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
   std::lock_guard<std::mutex> lock(mu);
@@ -98,6 +101,27 @@ const char* kg_status_str(kg_status s) {
     case KG_ERR_INTERNAL: return "internal limit reached";
   }
   return "unknown status";
+}
+
+kg_status kg_shutdown(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return KG_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return KG_ERR_CUDA;
+  {
+    std::lock_guard<std::mutex> lock(g_words_mu);
+    auto it = g_words.find(dev);
+    if (it != g_words.end()) {
+      cudaFree(it->second);
+      g_words.erase(it);
+    }
+  }
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) != cudaSuccess) return KG_ERR_CUDA;
+  uint64_t thr = 0;  // the pool's default: release at every synchronisation
+  if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr) != cudaSuccess ||
+      cudaMemPoolTrimTo(pool, 0) != cudaSuccess)
+    return KG_ERR_CUDA;
+  return KG_OK;
 }
 
 kg_status kg_last_error(void* stream) {

@@ -569,4 +569,9 @@ kg_status kg_gnp_undirected(uint64_t n, double p, uint64_t seed, uint32_t chunks
   return kg_gnp_ex(1, n, p, seed, chunks, K_LEAF, id_bytes, d_out, cap_edges, d_count, stream);
 }
 
+kg_status kg_gnp_size(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
+                      uint64_t* d_count, void* stream) {
+  return kg_gnp_count(undirected, n, p, seed, chunks, K_LEAF, d_count, stream);
+}
+
 }  // extern "C"

@@ -86,6 +86,28 @@ def test_argument_errors(kg):
     kg.check_device_error()
 
 
+def test_shutdown_releases_state_and_calls_still_work(kg):
+    """kg_shutdown frees the error word and trims the cached scratch; a call
+    after it makes that state again and returns the same graph."""
+    import torch
+    a = kg.gnm_directed(5000, 40000, 3, 8, id_bytes=4)
+    kg.check_device_error()
+    a = a.cpu()
+    kg.kg_shutdown()
+    b = kg.gnm_directed(5000, 40000, 3, 8, id_bytes=4)
+    kg.check_device_error()
+    assert torch.equal(a, b.cpu())
+    kg.kg_shutdown()
+    kg.kg_shutdown()  # idempotent
+    # the error word is made again: a capacity error found on the device
+    s = kg._stream_ptr(None)
+    out = torch.zeros((100, 2), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    kg.kg_gnp_ex(0, 2000, 0.01, 1, 4, 1024, 4, out.data_ptr(), 100, cnt.data_ptr(), s)
+    assert kg.kg_last_error(s) == kg.KG_ERR_CAPACITY
+    assert kg.kg_last_error(s) == kg.KG_OK
+
+
 def test_repeatable_and_stream_independent(kg):
     import torch
     n, m, P = 50000, 300000, 9

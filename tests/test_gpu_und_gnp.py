@@ -110,6 +110,27 @@ def test_gnp_zero_and_capacity(kg):
     assert L.kg_gnm_undirected(10, 5, 1, 2, 4, out.data_ptr(), 9, s) == kg.KG_ERR_CAPACITY
 
 
+@pytest.mark.parametrize("und,n,p,P", [(False, 3000, 0.01, 7), (True, 5000, 0.003, 31),
+                                        (True, 1, 0.5, 1), (False, 100, 0.0, 4)])
+def test_gnp_size_is_what_the_default_generators_write(kg, und, n, p, P):
+    """kg_gnp_size sizes kg_gnp_directed / kg_gnp_undirected exactly, and the
+    output sized by it holds the whole list."""
+    import torch
+    s = kg._stream_ptr(None)
+    size = torch.full((1,), 77, dtype=torch.int64, device="cuda")
+    kg.kg_gnp_size(int(und), n, p, 9, P, size.data_ptr(), s)
+    k = int(size.item())
+    out = torch.zeros((max(k, 1), 2), dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    f = kg.lib().kg_gnp_undirected if und else kg.lib().kg_gnp_directed
+    assert f(n, p, 9, P, 4, out.data_ptr(), k, cnt.data_ptr(), s) == kg.KG_OK
+    assert kg.kg_last_error(s) == kg.KG_OK
+    assert int(cnt.item()) == k
+    ref, rcnt = kg.gnp(und, n, p, 9, P, id_bytes=4)
+    assert int(rcnt.item()) == k
+    assert torch.equal(out[:k].cpu(), ref[:k].cpu())
+
+
 # ---------------------------------------------------------------- G(n,p), binomial chunk counts
 
 GNPB_CASES = [
