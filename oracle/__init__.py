@@ -21,7 +21,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["or_rng.c", "or_math.c", "or_variates.c", "or_er.c"]
+_SOURCES = ["or_rng.c", "or_math.c", "or_variates.c", "or_er.c", "or_rgg.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -102,6 +102,19 @@ def lib():
             L.or_gnp_binomial_counts.restype = i32
             L.or_gnp_binomial.argtypes = [i32, u64, dbl, u64, u32, u32, u32, p64, p64, u64, p64]
             L.or_gnp_binomial.restype = i32
+            pi32 = ctypes.POINTER(ctypes.c_int)
+            L.or_rgg_grid_level.argtypes = [i32, u64, dbl, pi32]
+            L.or_rgg_grid_level.restype = i32
+            L.or_rgg_cell_counts.argtypes = [i32, u64, dbl, u64, p64]
+            L.or_rgg_cell_counts.restype = i32
+            L.or_rgg_points.argtypes = [i32, u64, dbl, u64, p32]
+            L.or_rgg_points.restype = i32
+            L.or_rgg.argtypes = [i32, u64, dbl, u64, p64, p64, u64, p64]
+            L.or_rgg.restype = i32
+            L.or_rgg_rows.argtypes = [i32, u64, dbl, u64, u64, u64, p64, p64, u64, p64]
+            L.or_rgg_rows.restype = i32
+            L.or_rgg_digest.argtypes = [i32, u64, dbl, u64, p64, p64, p64]
+            L.or_rgg_digest.restype = i32
             L.or_edge_checksum.argtypes = [p64, p64, u64]
             L.or_edge_checksum.restype = u64
             L.or_outdegree_hist.argtypes = [p64, u64, u64, u64, p64]
@@ -278,6 +291,61 @@ def gnp_binomial(undirected, n, p, seed, P, k_leaf=K_LEAF, k_max=K_MAX, cap_hint
             continue
         _check(rc, "gnp_binomial")
         return u[:cnt.value], v[:cnt.value]
+
+
+# ---------------------------------------------------------------- RGG, Sec. 5
+
+def rgg_grid_level(dim, n, r) -> int:
+    """g of the 2^g-per-dimension cell grid."""
+    g = ctypes.c_int()
+    _check(lib().or_rgg_grid_level(dim, n, r, ctypes.byref(g)), "rgg_grid_level")
+    return g.value
+
+
+def rgg_cell_counts(dim, n, r, seed) -> np.ndarray:
+    """Points per cell, row-major cell order (dimension 0 fastest)."""
+    cnt = np.zeros(1 << (dim * rgg_grid_level(dim, n, r)), dtype=np.uint64)
+    _check(lib().or_rgg_cell_counts(dim, n, r, seed, _p64(cnt)), "rgg_cell_counts")
+    return cnt
+
+
+def rgg_points(dim, n, r, seed) -> np.ndarray:
+    """(n, dim) uint32 fixed-point coordinates (x 2^-32)."""
+    x = np.zeros((max(n, 1), dim), dtype=np.uint32)
+    _check(lib().or_rgg_points(dim, n, r, seed,
+                               x.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))), "rgg_points")
+    return x[:n]
+
+
+def rgg_rows(dim, n, r, seed, u_lo, u_hi, cap_hint=None):
+    """Entries of the rows of vertices [u_lo, u_hi), sorted by (u, v)."""
+    L = lib()
+    cap = cap_hint if cap_hint is not None else 1 << 16
+    while True:
+        u = np.zeros(max(cap, 1), dtype=np.uint64)
+        v = np.zeros(max(cap, 1), dtype=np.uint64)
+        cnt = ctypes.c_uint64()
+        rc = L.or_rgg_rows(dim, n, r, seed, u_lo, u_hi, _p64(u), _p64(v), cap, ctypes.byref(cnt))
+        if rc == 3:
+            cap = cnt.value
+            continue
+        _check(rc, "rgg_rows")
+        return u[:cnt.value], v[:cnt.value]
+
+
+def rgg(dim, n, r, seed, cap_hint=None):
+    """All entries of RGG(n, r) (both directions), sorted by (u, v)."""
+    return rgg_rows(dim, n, r, seed, 0, n, cap_hint)
+
+
+def rgg_digest(dim, n, r, seed):
+    """(entries, digest, degree histogram[65]) without storing the edges."""
+    e = ctypes.c_uint64()
+    d = ctypes.c_uint64()
+    h = np.zeros(65, dtype=np.uint64)
+    _check(lib().or_rgg_digest(dim, n, r, seed, ctypes.byref(e), ctypes.byref(d), _p64(h)),
+           "rgg_digest")
+    return e.value, d.value, h
 
 
 def edge_checksum(u, v) -> int:

@@ -78,6 +78,23 @@ int or_gnp_binomial(int undirected, uint64_t n, double p, uint64_t seed, uint32_
                     uint32_t k_leaf, uint32_t k_max, uint64_t *u, uint64_t *v, uint64_t cap,
                     uint64_t *count);
 
+/* ---- random geometric graph RGG(n, r), d = 2 or 3, Sec. 5 (see or_rgg.c) ---- */
+/* g: the grid has 2^g cells per dimension */
+int or_rgg_grid_level(int dim, uint64_t n, double r, int *g);
+/* points per cell, cells in row-major order (dimension 0 fastest), 2^(dim g) entries */
+int or_rgg_cell_counts(int dim, uint64_t n, double r, uint64_t seed, uint64_t *cnt);
+/* fixed-point coordinates (x 2^-32), n x dim, vertex-major */
+int or_rgg_points(int dim, uint64_t n, double r, uint64_t seed, uint32_t *coords);
+/* all entries (both directions), sorted by (u, v); *count = entries */
+int or_rgg(int dim, uint64_t n, double r, uint64_t seed, uint64_t *u, uint64_t *v, uint64_t cap,
+           uint64_t *count);
+/* the rows of vertices [u_lo, u_hi) */
+int or_rgg_rows(int dim, uint64_t n, double r, uint64_t seed, uint64_t u_lo, uint64_t u_hi,
+                uint64_t *u, uint64_t *v, uint64_t cap, uint64_t *count);
+/* entry count, digest (as or_edge_checksum) and degree histogram, without storing edges */
+int or_rgg_digest(int dim, uint64_t n, double r, uint64_t seed, uint64_t *entries,
+                  uint64_t *digest, uint64_t hist[65]);
+
 /* ---- order-independent edge-list digest ---- */
 uint64_t or_edge_checksum(const uint64_t *u, const uint64_t *v, uint64_t count);
 /* out-degree histogram over vertices [row_lo, row_hi): hist[d] for d<64, hist[64] for d>=64.
