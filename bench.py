@@ -234,6 +234,37 @@ def undirected_at_scale(kg, reps=2, ranges=256):
             "note": "each range regenerates the chunks of its row and column blocks"}
 
 
+def rgg_workload(kg, dim, n, deg, s):
+    """RGG(n, r) with r giving `deg` expected neighbours: time of one kg_rgg
+    call, entries/s, edge-write GB/s and the candidate pairs tested per second
+    (both passes)."""
+    import math
+    import torch
+    vol = math.pi if dim == 2 else 4 * math.pi / 3
+    r = (deg / (vol * (n - 1))) ** (1 / dim)
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    kg.kg_rgg_count(dim, n, r, 1, cnt.data_ptr(), s)
+    k = int(cnt.item())
+    out = torch.empty((k, 2), dtype=torch.int32, device="cuda")
+    kg.kg_profile_begin()
+    reps, warm = 5, 2
+    ms = _timed(lambda: kg.kg_rgg(dim, n, r, 1, 4, out.data_ptr(), k, cnt.data_ptr(), None, s),
+                reps, warm=warm)
+    prof = kg.kg_profile_end()
+    kg.check_device_error()
+    g = kg.rgg_grid(dim, n, r)
+    side = 2.0 ** -g
+    # expected candidates per vertex: points in the cells meeting its +-r box
+    cand = n * (side + 2 * r) ** dim
+    del out
+    return {"ms": ms, "r": r, "grid_cells": 1 << (dim * g), "entries": k,
+            "entries_per_s": k / ms * 1e3, "write_GBps": k * 8 / ms / 1e6,
+            "candidate_tests_per_s_est": 2 * n * cand / ms * 1e3,
+            "kernel_ms_per_call": {c: round(prof[c][0] / (reps + warm), 4)
+                                   for c in ("rgg", "scan") if prof[c][1]},
+            "bound": "integer ALU (distance tests of the count and emit passes)"}
+
+
 def other_workloads(kg, serve_requests=1000):
     """The other configurations, each measured briefly on the same GPU."""
     import torch
@@ -270,6 +301,12 @@ def other_workloads(kg, serve_requests=1000):
         "ms": ms, "entries": kb, "entries_per_s": kb / ms * 1e3, "write_GBps": kb * 8 / ms / 1e6}
     del out, cnt
     kg.check_device_error()
+    # random geometric graphs (Sec. 5): n = 2^26 points, average degree 16,
+    # uint32 ids, both directions; sized once by the count pass, then timed
+    # whole (cell tree, points, count pass, scan, emit pass)
+    for dim in (2, 3):
+        res[f"rgg{dim}d_n2e26_avgdeg16"] = rgg_workload(kg, dim, 1 << 26, 16.0, s)
+    torch.cuda.empty_cache()
     # undirected G(n,m) at scale by row blocks (Sec. 4.2): n = 2^32, m = 2^32
     # (2^33 entries, uint64 ids, 128 GiB), 4096 x 4096 chunk matrix, 256 ranges of
     # 16 row blocks, each with per-block digests and degree histograms

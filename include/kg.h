@@ -292,6 +292,40 @@ kg_status kg_server_pending(const kg_server* server, uint32_t* sizing, uint32_t*
                             uint32_t* running, uint64_t* bytes_in_use);
 kg_status kg_server_destroy(kg_server* server);
 
+/*
+ * Random geometric graph RGG(n, r), Sec. 5: n points uniform in the unit
+ * square (dim = 2) or cube (dim = 3), an edge between every two points at
+ * Euclidean distance <= r.  Coordinates are 32-bit fixed point (the integer x
+ * stands for x 2^-32); with R = floor(r 2^32), {u, v} is an edge iff
+ * sum_k (x_k(u) - x_k(v))^2 <= R^2, decided in exact integer arithmetic.
+ * The points are placed as in Sec. 5: a grid of 2^g cells per dimension
+ * (side 2^(32-g) >= R, at most n cells; kg_rgg_grid), the cell counts from
+ * the recursive split of the cube into its 2^d subcubes (each split as d
+ * halvings drawing Binomial(c, 1/2) from the stream of its tree node), and
+ * the points of a cell from the stream of that cell.  Vertex ids follow the
+ * cells in row-major order (dimension 0 fastest), then the order in which a
+ * cell's points are drawn.  The output is a pure function of (dim, n, r,
+ * seed).
+ *   dim in {2, 3}; 0 <= r <= 1/2 (else KG_ERR_ARG); n < 2^32 (else
+ *   KG_ERR_RANGE).
+ */
+/* g of the grid (host only, synchronous). */
+kg_status kg_rgg_grid(int dim, uint64_t n, double r, int* g_out);
+/* Points per cell: d_counts (device, 2^(dim g) uint64, row-major cells). */
+kg_status kg_rgg_cell_counts(int dim, uint64_t n, double r, uint64_t seed, uint64_t* d_counts,
+                             void* stream);
+/* Exact number of entries kg_rgg writes (twice the edge count), to *d_count. */
+kg_status kg_rgg_count(int dim, uint64_t n, double r, uint64_t seed, uint64_t* d_count,
+                       void* stream);
+/* All edges in both directions, sorted by (u, v), as id_bytes-wide pairs in
+ * d_out (at most cap_entries of them; more set the error word to
+ * KG_ERR_CAPACITY and are dropped); *d_count = entries.  d_coords (device,
+ * optional) receives the n x dim fixed-point coordinates, vertex-major.
+ * Scratch: about 4 dim n + 24 n + 12 cells bytes from the stream-ordered
+ * pool. */
+kg_status kg_rgg(int dim, uint64_t n, double r, uint64_t seed, int id_bytes, void* d_out,
+                 uint64_t cap_entries, uint64_t* d_count, uint32_t* d_coords, void* stream);
+
 /* Order-independent digest of an edge list (see kg_gnm_directed_range):
  * *d_digest = sum of splitmix64(u xor rotl64(v, 32)) over `count` pairs. */
 kg_status kg_edge_digest(const void* d_edges, uint64_t count, int id_bytes, uint64_t* d_digest,
@@ -319,9 +353,10 @@ kg_status kg_shutdown(void);
  * for those events and returns, per kernel class, the summed milliseconds and
  * the number of launches (arrays of KG_PROF_CLASSES entries, host memory).
  * Classes: 0 chunk split tree, 1 tile tree, 2 scan, 3 leaf sampler/emitter,
- * 4 digest, 5 G(n,p) tile sampler, 6 undirected assembly, 7 other.
+ * 4 digest, 5 G(n,p) tile sampler, 6 undirected assembly, 7 other,
+ * 8 random geometric graph.
  */
-#define KG_PROF_CLASSES 8
+#define KG_PROF_CLASSES 9
 unsigned long long kg_launch_count(void);
 kg_status kg_profile_begin(void);
 kg_status kg_profile_end(double* ms, unsigned long long* launches);

@@ -68,6 +68,10 @@ def lib() -> ctypes.CDLL:
                 "kg_edge_digest": [vp, u64, i32, vp, vp],
                 "kg_last_error": [vp],
                 "kg_gnp_size": [i32, u64, dbl, u64, u32, vp, vp],
+                "kg_rgg": [i32, u64, dbl, u64, i32, vp, u64, vp, vp, vp],
+                "kg_rgg_count": [i32, u64, dbl, u64, vp, vp],
+                "kg_rgg_cell_counts": [i32, u64, dbl, u64, vp, vp],
+                "kg_rgg_grid": [i32, u64, dbl, ctypes.POINTER(ctypes.c_int)],
                 "kg_shutdown": [],
                 "kg_gnm_directed_noalloc": [u64, u64, u64, u32, i32, vp, u64, vp, vp],
             }
@@ -217,7 +221,8 @@ def kg_last_error(stream) -> int:
     return lib().kg_last_error(stream)
 
 
-PROF_CLASSES = ("chunk_tree", "tile_tree", "scan", "leaf", "digest", "gnp_tile", "assembly", "other")
+PROF_CLASSES = ("chunk_tree", "tile_tree", "scan", "leaf", "digest", "gnp_tile", "assembly", "other",
+                "rgg")
 
 
 def kg_launch_count() -> int:
@@ -289,6 +294,52 @@ def kg_gnp_count(undirected, n, p, seed, chunks, k_leaf, d_count, stream):
 
 def kg_gnp_size(undirected, n, p, seed, chunks, d_count, stream):
     return _call("kg_gnp_size", int(undirected), n, p, seed, chunks, d_count, stream)
+
+
+def kg_rgg(dim, n, r, seed, id_bytes, d_out, cap_entries, d_count, d_coords, stream):
+    return _call("kg_rgg", dim, n, r, seed, id_bytes, d_out, cap_entries, d_count, d_coords,
+                 stream)
+
+
+def kg_rgg_count(dim, n, r, seed, d_count, stream):
+    return _call("kg_rgg_count", dim, n, r, seed, d_count, stream)
+
+
+def kg_rgg_cell_counts(dim, n, r, seed, d_counts, stream):
+    return _call("kg_rgg_cell_counts", dim, n, r, seed, d_counts, stream)
+
+
+def rgg_grid(dim, n, r) -> int:
+    """g of the 2^g-per-dimension cell grid of RGG(n, r) (Sec. 5)."""
+    g = ctypes.c_int()
+    _call("kg_rgg_grid", dim, n, r, ctypes.byref(g))
+    return g.value
+
+
+def rgg_cell_counts(dim, n, r, seed=1, stream=None, device="cuda"):
+    """Points per cell (row-major cells) as an int64 tensor."""
+    import torch
+    out = torch.zeros(1 << (dim * rgg_grid(dim, n, r)), dtype=torch.int64, device=device)
+    kg_rgg_cell_counts(dim, n, r, seed, out.data_ptr(), _stream_ptr(stream))
+    return out
+
+
+def rgg(dim, n, r, seed=1, id_bytes=4, coords=False, stream=None, device="cuda"):
+    """RGG(n, r) (Sec. 5): the (entries, 2) tensor of both directions sorted by
+    (u, v), sized exactly by a count pass first; with coords=True also the
+    (n, dim) int32 tensor holding the uint32 fixed-point coordinates."""
+    import torch
+    s = _stream_ptr(stream)
+    cnt = torch.zeros(1, dtype=torch.int64, device=device)
+    kg_rgg_count(dim, n, r, seed, cnt.data_ptr(), s)
+    k = int(cnt.item())
+    out = _empty_edges(max(k, 1), id_bytes, device)
+    xy = torch.zeros((max(n, 1), dim), dtype=torch.int32, device=device) if coords else None
+    kg_rgg(dim, n, r, seed, id_bytes, out.data_ptr(), k, cnt.data_ptr(),
+           xy.data_ptr() if coords else None, s)
+    if coords:
+        return out[:k], xy[:n]
+    return out[:k]
 
 
 def kg_shutdown():

@@ -2,7 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
-#define KG_PROF_CLASSES 8
+#define KG_PROF_CLASSES 9
 
 namespace kg {
 enum ProfClass : int {
@@ -14,6 +14,7 @@ enum ProfClass : int {
   PROF_GNP = 5,
   PROF_ASSEMBLY = 6,
   PROF_OTHER = 7,
+  PROF_RGG = 8,
 };
 
 // Counts one launch; when profiling is on, brackets it with events on `s`.
