@@ -113,13 +113,29 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Points packed per vertex: (x, y) or (x, y, z, 0).
+template <int DIM>
+struct PtOf;
+template <>
+struct PtOf<2> {
+  using T = uint2;
+  __device__ __forceinline__ static uint32_t at(const uint2& p, int k) { return k ? p.y : p.x; }
+};
+template <>
+struct PtOf<3> {
+  using T = uint4;
+  __device__ __forceinline__ static uint32_t at(const uint4& p, int k) {
+    return k == 0 ? p.x : (k == 1 ? p.y : p.z);
+  }
+};
+
 // One block per group of 256 consecutive cells: the group's points are spread
 // over the block's threads, each finding its cell by a binary search over the
 // group's starts in shared memory.
 template <int DIM>
 __global__ void __launch_bounds__(256)
-    rgg_points(const uint64_t* __restrict__ S, int g, uint64_t seed, uint64_t n,
-               uint32_t* __restrict__ X, uint32_t* __restrict__ coords) {
+    rgg_points(const uint64_t* __restrict__ S, int g, uint64_t seed,
+               typename PtOf<DIM>::T* __restrict__ P, uint32_t* __restrict__ coords) {
   __shared__ uint64_t s_start[RGG_CELLS_PER_BLOCK + 1];
   const uint64_t cells = uint64_t(1) << (DIM * g);
   const uint32_t mask = (uint32_t(1) << g) - 1;
@@ -147,12 +163,16 @@ __global__ void __launch_bounds__(256)
       const uint64_t z = morton_of<DIM>(c, g);
       uint32_t w[4];
       philox10(uint32_t(j), uint32_t(z), uint32_t(z >> 32), TAG_RGG_POINT, k0, k1, w);
+      uint32_t x[3] = {0, 0, 0};
 #pragma unroll
       for (int k = 0; k < DIM; ++k) {
-        const uint32_t x = uint32_t((uint64_t(c[k]) << (32 - g)) | (w[k] >> g));
-        X[uint64_t(k) * n + p] = x;
-        if (coords) coords[p * DIM + k] = x;
+        x[k] = uint32_t((uint64_t(c[k]) << (32 - g)) | (w[k] >> g));
+        if (coords) coords[p * DIM + k] = x[k];
       }
+      if constexpr (DIM == 2)
+        P[p] = make_uint2(x[0], x[1]);
+      else
+        P[p] = make_uint4(x[0], x[1], x[2], 0u);
     }
     __syncthreads();
   }
@@ -168,52 +188,60 @@ __device__ __forceinline__ void rgg_store(Id* out, uint64_t i, uint64_t u, uint6
 }
 
 // Count pass (EMIT = false: deg[u] = entries of row u) or emit pass (the
-// entries of row u at rowptr[u] ..), one thread per vertex.
+// entries of row u at rowptr[u] ..), one thread per vertex: the cells that
+// meet the box [x(u) - R, x(u) + R]^d, row by row, their points in id order.
+// Ids fit 32 bits (n < 2^32) and every coordinate difference that matters is
+// <= R <= 2^31, so only the sum of squares needs 64 bits.
 template <int DIM, bool EMIT, class Id>
 __global__ void __launch_bounds__(256)
-    rgg_edges(const uint32_t* __restrict__ X, uint64_t n, int g, uint64_t R,
+    rgg_edges(const typename PtOf<DIM>::T* __restrict__ P, uint32_t n, int g, uint32_t R,
               const uint64_t* __restrict__ S, unsigned long long* __restrict__ deg,
               const uint64_t* __restrict__ rowptr, Id* __restrict__ out, uint64_t cap,
               int* err) {
-  const int64_t G = int64_t(1) << g;
+  using Pt = typename PtOf<DIM>::T;
+  const int G = 1 << g;
   const int sh = 32 - g;
-  const uint64_t R2 = R * R;
-  for (uint64_t u = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; u < n;
-       u += uint64_t(gridDim.x) * blockDim.x) {
+  const uint64_t R2 = uint64_t(R) * R;
+  for (uint64_t uu = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; uu < n;
+       uu += uint64_t(gridDim.x) * blockDim.x) {
+    const uint32_t u = uint32_t(uu);
+    const Pt pu = P[u];
     uint32_t xu[DIM];
-    int64_t clo[3] = {0, 0, 0}, chi[3] = {0, 0, 0};
+    int lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
-      xu[k] = X[uint64_t(k) * n + u];
-      const int64_t a = int64_t(xu[k]) - int64_t(R), b = int64_t(xu[k]) + int64_t(R);
-      clo[k] = a < 0 ? 0 : (a >> sh);
-      chi[k] = (b >> sh) < G - 1 ? (b >> sh) : G - 1;
+      xu[k] = PtOf<DIM>::at(pu, k);
+      const int64_t a = int64_t(xu[k]) - R, b = int64_t(xu[k]) + R;
+      lo[k] = a < 0 ? 0 : int(a >> sh);
+      hi[k] = int(b >> sh) < G - 1 ? int(b >> sh) : G - 1;
     }
-    uint64_t pos = EMIT ? rowptr[u] : 0, cnt = 0;
-    for (int64_t c2 = clo[2]; c2 <= chi[2]; ++c2)
-      for (int64_t c1 = clo[1]; c1 <= chi[1]; ++c1) {
-        const uint64_t row = uint64_t(c2 * G + c1) * uint64_t(G);
-        const uint64_t v0 = S[row + clo[0]], v1 = S[row + chi[0] + 1];
-        for (uint64_t v = v0; v < v1; ++v) {
+    uint64_t pos = EMIT ? rowptr[u] : 0;
+    uint32_t cnt = 0;
+    for (int d2 = lo[2]; d2 <= hi[2]; ++d2)
+      for (int d1 = lo[1]; d1 <= hi[1]; ++d1) {
+        const uint64_t row = (uint64_t(d2) * G + d1) * uint64_t(G);
+        const uint32_t v0 = uint32_t(S[row + lo[0]]), v1 = uint32_t(S[row + hi[0] + 1]);
+        for (uint32_t v = v0; v < v1; ++v) {
+          const Pt pv = P[v];
+          uint32_t m = 0;
           uint64_t s2 = 0;
-          bool near = v != u;
 #pragma unroll
           for (int k = 0; k < DIM; ++k) {
-            const uint32_t xv = X[uint64_t(k) * n + v];
-            const uint32_t d = xu[k] > xv ? xu[k] - xv : xv - xu[k];
-            near = near && d <= R;
-            s2 += uint64_t(d) * d;  // may wrap when d > R; then `near` is false
+            const uint32_t dk = __usad(xu[k], PtOf<DIM>::at(pv, k), 0u);  // |x_k(u) - x_k(v)|
+            m = m > dk ? m : dk;
+            s2 += uint64_t(dk) * dk;  // may wrap when dk > R; then m > R
           }
-          if (near && s2 <= R2) {
-            if (EMIT) {
+          const bool hit = (m <= R) & (s2 <= R2) & (v != u);
+          if (EMIT) {
+            if (hit) {
               if (pos < cap)
                 rgg_store(out, pos, u, v);
               else
                 set_error(err, ST_CAPACITY);
               ++pos;
-            } else {
-              ++cnt;
             }
+          } else {
+            cnt += hit;
           }
         }
       }
@@ -249,8 +277,9 @@ int rgg_run(const RggGrid& G, uint64_t seed, RggStop stop, int id_bytes, void* d
     if (launch_ok()) return ST_CUDA;
   }
   if (stop == RggStop::CELLS) return ST_OK;
+  using Pt = typename PtOf<DIM>::T;
   uint64_t* S = ws.alloc<uint64_t>(G.cells + 1);
-  uint32_t* X = ws.alloc<uint32_t>(uint64_t(DIM) * n);
+  Pt* P = ws.alloc<Pt>(n);
   unsigned long long* deg = ws.alloc<unsigned long long>(n);
   uint64_t* rowptr = ws.alloc<uint64_t>(n + 1);
   if (!ws.ok()) return ST_CUDA;
@@ -259,13 +288,14 @@ int rgg_run(const RggGrid& G, uint64_t seed, RggStop stop, int id_bytes, void* d
   {
     ProfScope ps(PROF_RGG, s);
     rgg_points<DIM><<<grid_for(G.cells, RGG_CELLS_PER_BLOCK, 152 * 8), 256, 0, s>>>(
-        S, G.g, seed, n, X, d_coords);
+        S, G.g, seed, P, d_coords);
     if (launch_ok()) return ST_CUDA;
   }
+  const unsigned eblocks = grid_for(n, 256, 152 * 16);
   {
     ProfScope ps(PROF_RGG, s);
-    rgg_edges<DIM, false, uint32_t><<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(
-        X, n, G.g, G.R, S, deg, nullptr, nullptr, 0, err);
+    rgg_edges<DIM, false, uint32_t><<<eblocks, 256, 0, s>>>(P, uint32_t(n), G.g, uint32_t(G.R), S,
+                                                             deg, nullptr, nullptr, 0, err);
     if (launch_ok()) return ST_CUDA;
   }
   st = scan_exclusive_u64(reinterpret_cast<const uint64_t*>(deg), rowptr, n, ws, s);
@@ -276,11 +306,13 @@ int rgg_run(const RggGrid& G, uint64_t seed, RggStop stop, int id_bytes, void* d
   if (stop == RggStop::COUNT) return ST_OK;
   ProfScope ps(PROF_RGG, s);
   if (id_bytes == 4)
-    rgg_edges<DIM, true, uint32_t><<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(
-        X, n, G.g, G.R, S, nullptr, rowptr, static_cast<uint32_t*>(d_out), cap, err);
+    rgg_edges<DIM, true, uint32_t><<<eblocks, 256, 0, s>>>(P, uint32_t(n), G.g, uint32_t(G.R), S,
+                                                            nullptr, rowptr,
+                                                            static_cast<uint32_t*>(d_out), cap, err);
   else
-    rgg_edges<DIM, true, uint64_t><<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(
-        X, n, G.g, G.R, S, nullptr, rowptr, static_cast<uint64_t*>(d_out), cap, err);
+    rgg_edges<DIM, true, uint64_t><<<eblocks, 256, 0, s>>>(P, uint32_t(n), G.g, uint32_t(G.R), S,
+                                                            nullptr, rowptr,
+                                                            static_cast<uint64_t*>(d_out), cap, err);
   return launch_ok();
 }
 

@@ -40,6 +40,7 @@ CASES = [
     (2, 1 << 20, r_for_degree(2, 1 << 20, 16), 12, 4),
     (3, 1 << 20, r_for_degree(3, 1 << 20, 16), 13, 4),
     (3, 6000, 0.5, 14, 4),        # 750 points per cell: FP64 splits above 1024, dense rows
+    (3, 9000, 0.5, 15, 4),        # neighbourhood above the shared-memory stage: global reads
 ]
 
 
