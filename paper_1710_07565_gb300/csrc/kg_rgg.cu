@@ -178,13 +178,14 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// One 8- or 16-byte store of the entry (u, v) at slot i.
+// One 8- or 16-byte store of the entry (u, v) at slot i, marked evict-first
+// so that the output stream does not push the points out of L2.
 template <class Id>
 __device__ __forceinline__ void rgg_store(Id* out, uint64_t i, uint64_t u, uint64_t v) {
   if (sizeof(Id) == 4)
-    reinterpret_cast<uint2*>(out)[i] = make_uint2(uint32_t(u), uint32_t(v));
+    __stcs(reinterpret_cast<uint2*>(out) + i, make_uint2(uint32_t(u), uint32_t(v)));
   else
-    reinterpret_cast<ulonglong2*>(out)[i] = make_ulonglong2(u, v);
+    __stcs(reinterpret_cast<ulonglong2*>(out) + i, make_ulonglong2(u, v));
 }
 
 // Count pass (EMIT = false: deg[u] = entries of row u) or emit pass (the
