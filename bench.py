@@ -136,10 +136,52 @@ def cpu_baseline(seconds=10.0, workers=None):
     dt = time.perf_counter() - t0
     edges = sum(r[0] for r in res)
     chunks = sum(r[1] for r in res)
+    # the plain single-threaded oracle on the same kind of chunks, in this process
+    t1 = time.perf_counter()
+    e1, c1 = _oracle_chunks((cnt, 0, 1, min(2.0, seconds / 4)))
+    dt1 = time.perf_counter() - t1
     return {"value": edges / dt, "unit": "edges/s", "cores": workers, "kind": "oracle",
             "sample": f"chunk split tree of all 2^16 chunks ({t_tree:.2f} s, one core) + "
                       f"{chunks} whole chunks ({edges} edges) with digest and histogram, "
-                      f"chunk-parallel on {workers} processes, {dt:.1f} s wall"}
+                      f"chunk-parallel on {workers} processes, {dt:.1f} s wall",
+            "single_thread_value": e1 / dt1,
+            "single_thread_sample": f"{c1} whole chunks ({e1} edges), one process, {dt1:.1f} s",
+            "cpu": _cpu_name()}
+
+
+def _cpu_name():
+    """The host CPU as /proc/cpuinfo names it (model name, else implementer/part)."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    for key in ("model name", "Model"):
+        for line in info:
+            if line.startswith(key):
+                return f"{platform.machine()} {line.split(':', 1)[1].strip()}"
+    parts = {line.split(":", 1)[0].strip(): line.split(":", 1)[1].strip()
+             for line in info if line.startswith(("CPU implementer", "CPU part"))}
+    return f"{platform.machine()} implementer {parts.get('CPU implementer', '?')} " \
+           f"part {parts.get('CPU part', '?')}"
+
+
+def write_peak_gbps():
+    """A plain store kernel's rate: torch's fill of an 8 GiB buffer, best of 5."""
+    import torch
+    buf = torch.empty(8 << 30, dtype=torch.uint8, device="cuda")
+    best = None
+    for _ in range(7):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        buf.fill_(1)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    del buf
+    return (8 << 30) / best / 1e6
 
 
 def run_reference(args, rank, world):
@@ -523,6 +565,7 @@ def main():
     bytes_per_launch = M_EDGES * 16 / SLABS  # algorithmic: the edges written by one slab launch
     achieved = bytes_per_launch / per_launch_s / 1e9
     clocks = clk.summary()
+    wpeak = write_peak_gbps()
 
     if rank != 0:
         return
@@ -538,7 +581,9 @@ def main():
                      "frac": achieved / peak,
                      "traffic": LEAF_TRAFFIC_PER_EDGE * M_EDGES / SLABS,
                      "kernel": "leaf_fast_kernel (Floyd draws, shared-memory sort, emit, digest)",
-                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+                     "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "write_peak_GBps": wpeak, "frac_of_write_peak": achieved / wpeak,
+                     "frac_of_nominal_7900": achieved / 7900.0},
         "kernel_ms": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
         "kernel_launches_per_step": {k: v[1] // args.steps for k, v in prof.items() if v[1]},
         "e2e": {"value": e2e, "unit": "edges/s", "h2d_bytes_per_step": 0,
