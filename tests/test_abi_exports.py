@@ -19,7 +19,8 @@ def test_header_declares_the_entry_points():
     for must in ("kg_gnm_directed", "kg_gnm_undirected", "kg_gnp_directed", "kg_gnp_undirected",
                  "kg_gnm_directed_range", "kg_gnm_undirected_rows", "kg_gnp_binomial",
                  "kg_batch_run", "kg_server_poll", "kg_edge_digest", "kg_last_error",
-                 "kg_status_str", "kg_gnm_directed_noalloc"):
+                 "kg_status_str", "kg_gnm_directed_noalloc", "kg_rgg", "kg_rgg_count",
+                 "kg_rgg_cell_counts", "kg_rgg_grid", "kg_gnp_size", "kg_shutdown"):
         assert must in names, must
 
 
@@ -33,3 +34,24 @@ def test_library_exports_every_declared_function():
     lib.kg_status_str.restype = ctypes.c_char_p
     lib.kg_status_str.argtypes = [ctypes.c_int]
     assert lib.kg_status_str(0) and lib.kg_status_str(3)
+
+
+def test_rgg_grid_level_matches_the_oracle(orc):
+    """kg_rgg_grid is host logic (no device): the library's grid rule and the
+    oracle's, written separately, agree over sizes, radii and both limits."""
+    import paper_1710_07565_gb300 as kg
+    lib = ctypes.CDLL(kg.build())
+    lib.kg_rgg_grid.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_double,
+                                ctypes.POINTER(ctypes.c_int)]
+    lib.kg_rgg_grid.restype = ctypes.c_int
+    g = ctypes.c_int()
+    radii = [0.0, 1e-9, 1e-6, 2 ** -17, 1e-4, 0.001, 0.01, 0.03, 0.1, 0.2, 0.25, 0.3, 0.5]
+    sizes = [0, 1, 3, 4, 7, 8, 63, 64, 1000, 4095, 4096, 10 ** 6, 1 << 26, (1 << 32) - 1]
+    for dim in (2, 3):
+        for n in sizes:
+            for r in radii:
+                assert lib.kg_rgg_grid(dim, n, r, ctypes.byref(g)) == 0
+                assert g.value == orc.rgg_grid_level(dim, n, r), (dim, n, r)
+    assert lib.kg_rgg_grid(4, 10, 0.1, ctypes.byref(g)) == kg.KG_ERR_ARG
+    assert lib.kg_rgg_grid(2, 10, 0.51, ctypes.byref(g)) == kg.KG_ERR_ARG
+    assert lib.kg_rgg_grid(2, 1 << 32, 0.1, ctypes.byref(g)) == kg.KG_ERR_RANGE
