@@ -119,3 +119,39 @@ def test_rgg_at_scale_digest_and_sampled_rows(kg, orc, dim):
         gu, gv = edges_np(t[a:b], 4)
         ou, ov = orc.rgg_rows(dim, n, r, seed, lo, hi)
         assert_same_edges(gu, gv, ou, ov, f"rows [{lo}, {hi})")
+
+
+def test_rgg_largest_ids_properties(kg):
+    """n = 2^31 points (ids up to 2^31 - 1 in uint32 output, 2^30 cells): no
+    oracle at this size, so what holds at any size: cell counts sum to n, rows
+    strictly sorted without self-loops, the edge set symmetric (equal digests
+    of the list and of its transpose), every entry within the radius."""
+    import torch
+    n, r, seed = 1 << 31, 1e-6, 3
+    assert kg.rgg_grid(2, n, r) == 15
+    cells = kg.rgg_cell_counts(2, n, r, seed)
+    kg.check_device_error()
+    assert int(cells.sum()) == n
+    del cells
+    t, xy = kg.rgg(2, n, r, seed, id_bytes=4, coords=True)
+    kg.check_device_error()
+    k = t.shape[0]
+    assert k % 2 == 0 and k > 1000
+    u = t[:, 0].to(torch.int64) & 0xffffffff
+    v = t[:, 1].to(torch.int64) & 0xffffffff
+    assert int(u.max()) >= 1 << 30
+    assert bool((u != v).all())
+    key = u * n + v
+    assert bool((key[1:] > key[:-1]).all())
+    s = kg._stream_ptr(None)
+    d1 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    d2 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    tt = torch.stack((t[:, 1], t[:, 0]), dim=1).contiguous()
+    kg.kg_edge_digest(t.data_ptr(), k, 4, d1.data_ptr(), s)
+    kg.kg_edge_digest(tt.data_ptr(), k, 4, d2.data_ptr(), s)
+    assert int(d1.item()) == int(d2.item())
+    R = int(r * 2 ** 32)
+    pu = xy[u].to(torch.int64) & 0xffffffff
+    pv = xy[v].to(torch.int64) & 0xffffffff
+    d = pu - pv
+    assert int((d * d).sum(dim=1).max()) <= R * R
