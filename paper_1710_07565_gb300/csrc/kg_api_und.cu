@@ -63,7 +63,8 @@ static int run_quadtree(const UndParams& up, uint64_t seed, uint64_t* chunk_cnt,
   for (int l = 0; l <= up.D; ++l) {
     const uint64_t bound = (l < 16) ? ((uint64_t(1) << l) * ((uint64_t(1) << l) + 1) / 2) : C;
     ProfScope ps(PROF_CHUNK_TREE, s);
-    quad_level<<<grid_for(bound < C ? bound : C, 256, 152 * 8), 256, 0, s>>>(
+    // one-warp blocks spread the few FP64-bound nodes of the top levels over the SMs
+    quad_level<<<grid_for(bound < C ? bound : C, 32, 152 * 64), 32, 0, s>>>(
         rb, seed, (l & 1) ? L1 : L0, counts + l, (l & 1) ? L0 : L1, counts + l + 1, chunk_cnt, err);
     if (launch_ok()) return ST_CUDA;
   }
@@ -320,7 +321,8 @@ template <class Geom>
 static int gnpb_counts(const Geom& g, uint64_t C, double p, uint64_t seed, uint64_t* cnt,
                        cudaStream_t s, int* err) {
   ProfScope ps(PROF_CHUNK_TREE, s);
-  gnp_chunk_counts<Geom><<<grid_for(C, 128, 152 * 16), 128, 0, s>>>(g, C, p, seed, cnt, err);
+  // one-warp blocks: a few hundred FP64 binomials spread over the SMs
+  gnp_chunk_counts<Geom><<<grid_for(C, 32, 152 * 64), 32, 0, s>>>(g, C, p, seed, cnt, err);
   return launch_ok();
 }
 

@@ -85,7 +85,9 @@ int run_chunks(const Geom& g, uint64_t c_begin, uint64_t C, const uint64_t* leve
       uint64_t* out = (level & 1) ? B : A;
       const uint64_t nodes = C << level;
       ProfScope ps(PROF_TILE_TREE, s);
-      tile_tree_level<Geom><<<grid_for(nodes, 256, 152 * 16), 256, 0, s>>>(
+      // one-warp blocks: the top levels hold a few thousand FP64-bound nodes,
+      // which 256-thread blocks would pile onto a few SMs
+      tile_tree_level<Geom><<<grid_for(nodes, 32, 152 * 64), 32, 0, s>>>(
           g, c_begin, C, d, level, seed, in, out, err);
       if (launch_ok()) return ST_CUDA;
       in = out;
