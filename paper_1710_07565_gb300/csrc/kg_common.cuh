@@ -20,12 +20,8 @@ __device__ __forceinline__ void set_error(int* err, int code) {
   if (err) atomicCAS(err, 0, code);
 }
 
-// Chunk boundary r_c = floor(c n / P) ("sections of size roughly n/P", Sec. 4.2).
-__host__ __device__ __forceinline__ uint64_t row_bound(uint64_t n, uint32_t P, uint64_t c) {
-  return uint64_t((u128(c) * n) / P);
-}
-
-// r_c without 128-bit division: with n = qP + r, floor(cn/P) = cq + floor(cr/P)
+// Chunk boundary r_c = floor(c n / P) ("sections of size roughly n/P",
+// Sec. 4.2), without 128-bit division: with n = qP + r, floor(cn/P) = cq + floor(cr/P)
 // and cr < 2^48 for c <= P <= 2^24, divided through an invariant multiplier.
 struct RowBounds {
   uint64_t n, q, r;
