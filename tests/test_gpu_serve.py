@@ -71,7 +71,9 @@ def _alone(kg, req):
 
 
 def test_alone_equals_in_mix_under_a_tight_budget(kg):
-    reqs = _small_requests(80)
+    """200 requests served together under a budget far below their total
+    output, each equal (entry count and digest) to the same request alone."""
+    reqs = _small_requests(200)
     sizes = [_alone(kg, r) for r in reqs]
     biggest = max(k for k, _ in sizes) * 8
     budget = max(biggest * 3, 1 << 20)            # far below the total: admission must wait
