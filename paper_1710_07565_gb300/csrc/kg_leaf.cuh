@@ -282,6 +282,10 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
         }
     }
     __syncthreads();
+    // every thread is past the previous tile: its descriptor slot takes the
+    // next tile's (DIGEST: the barriers below publish it, so the tile ends
+    // without one of its own)
+    if (DIGEST && tn < ntiles) stage(tn, cur ^ 1);
     // ---- 3. exclusive scan of the packed counts: thread tid owns words
     // [tid*per, tid*per + per), per = nb / (2 FAST_THREADS) in {4, 8, ...}
     {
@@ -587,8 +591,11 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
       for (int b = tid; b < 65; b += FAST_THREADS)
         if (bh[b]) atomicAdd(&dig.hist[cl * 65 + b], (unsigned long long)bh[b]);
     }
-    if (tn < ntiles) stage(tn, cur ^ 1);
-    __syncthreads();
+    if constexpr (!DIGEST) {
+      // the emission read A / D, which the next tile's draws overwrite
+      if (tn < ntiles) stage(tn, cur ^ 1);
+      __syncthreads();
+    }
   }
 }
 
