@@ -413,6 +413,13 @@ def other_workloads(kg, serve_requests=1000):
         "entries_per_s": ent / dt2, "p50_ms": lat[len(lat) // 2], "p99_ms": lat[int(0.99 * (len(lat) - 1))],
         "ok": all(r["status"] == 0 for r in done),
         "sample": f"first {len(reqs)} requests of the seeded 100k-request stream"}
+    # served vs one request after another through the plain entry points: the
+    # first 300 requests, and the first 300 of those with n <= 2^18 (the part
+    # of the stream where a single request leaves the GPU mostly idle)
+    res["serving"]["vs_sequential"] = serving_vs_sequential(kg, base[:300], budget)
+    small = [r for r in workloads.serving_requests(4 * serve_requests, 1.0)
+             if r["n"] <= 1 << 18][:300]
+    res["serving"]["vs_sequential_n_le_2e18"] = serving_vs_sequential(kg, small, budget)
     # the same stream at 0.5x and 1.0x of the closed-loop capacity (first half)
     for frac in (0.5, 1.0):
         rq = workloads.serving_requests(serve_requests // 2, frac * cap_rps)
@@ -425,6 +432,58 @@ def other_workloads(kg, serve_requests=1000):
             "p50_ms": lt[len(lt) // 2], "p99_ms": lt[int(0.99 * (len(lt) - 1))],
             "ok": all(r["status"] == 0 for r in dn)}
     return res
+
+
+def _request_alone(kg, req, s):
+    """One serving request through the plain entry points, as a caller without
+    the serving loop would run it: exact output buffer (sized on the device
+    for G(n,p)), generation, digest, digest read back; returns (entries, digest)."""
+    import torch
+    dig = torch.zeros(1, dtype=torch.int64, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    und, n, seed, P = req["undirected"], req["n"], req["seed"], req["chunks"]
+    if req["model"] == "gnm":
+        k = 2 * req["m"] if und else req["m"]
+        out = torch.empty((max(k, 1), 2), dtype=torch.int32, device="cuda")
+        (kg.kg_gnm_undirected if und else kg.kg_gnm_directed)(n, req["m"], seed, P, 4,
+                                                              out.data_ptr(), k, s)
+    elif req["model"] == "gnp_binomial":
+        kg.kg_gnp_binomial_count(und, n, req["p"], seed, P, cnt.data_ptr(), s)
+        k = int(cnt.item())
+        out = torch.empty((max(k, 1), 2), dtype=torch.int32, device="cuda")
+        kg.kg_gnp_binomial(und, n, req["p"], seed, P, 4, out.data_ptr(), k, cnt.data_ptr(), s)
+    else:
+        kg.kg_gnp_count(und, n, req["p"], seed, P, 1024, cnt.data_ptr(), s)
+        k = int(cnt.item())
+        out = torch.empty((max(k, 1), 2), dtype=torch.int32, device="cuda")
+        kg.kg_gnp_ex(und, n, req["p"], seed, P, 1024, 4, out.data_ptr(), k, cnt.data_ptr(), s)
+    kg.kg_edge_digest(out.data_ptr(), k, 4, dig.data_ptr(), s)
+    d = int(dig.item()) & ((1 << 64) - 1)
+    del out
+    return k, d
+
+
+def serving_vs_sequential(kg, reqs, budget):
+    """The same requests served by the loop (closed, all queued at once) and
+    one after another through the plain entry points; equal digests required."""
+    import torch
+    s = torch.cuda.current_stream().cuda_stream
+    sub = [dict(r, arrival=0.0) for r in reqs]
+    kg.serve(sub[:8], budget, streams=8, realtime=False)  # warm-up
+    _request_alone(kg, sub[0], s)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    served = kg.serve(sub, budget, streams=8, realtime=False)
+    t_srv = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    alone = [_request_alone(kg, r, s) for r in sub]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    kg.check_device_error()
+    same = all((r["entries"], r["digest"]) == a for r, a in zip(served, alone))
+    return {"requests": len(sub), "served_requests_per_s": len(sub) / t_srv,
+            "sequential_requests_per_s": len(sub) / t_seq, "speedup": t_seq / t_srv,
+            "identical_output": same}
 
 
 def profile_case(kg, C):
