@@ -321,8 +321,8 @@ kg_status kg_rgg_count(int dim, uint64_t n, double r, uint64_t seed, uint64_t* d
  * d_out (at most cap_entries of them; more set the error word to
  * KG_ERR_CAPACITY and are dropped); *d_count = entries.  d_coords (device,
  * optional) receives the n x dim fixed-point coordinates, vertex-major.
- * Scratch: about 4 dim n + 24 n + 12 cells bytes from the stream-ordered
- * pool. */
+ * Scratch from the stream-ordered pool: 24 n (dim 2) or 32 n (dim 3) bytes
+ * (packed points, degrees, row offsets) plus 20 bytes per cell. */
 kg_status kg_rgg(int dim, uint64_t n, double r, uint64_t seed, int id_bytes, void* d_out,
                  uint64_t cap_entries, uint64_t* d_count, uint32_t* d_coords, void* stream);
 
