@@ -154,6 +154,18 @@ kg_status kg_gnp_ex(int undirected, uint64_t n, double p, uint64_t seed, uint32_
                     uint32_t k_leaf, int id_bytes, void* d_out, uint64_t cap_edges,
                     uint64_t* d_count, void* stream);
 
+/* Test and instrumentation hook of kg_gnp_ex (no counterpart in the paper):
+ * the skip walk of a tile stores its kept offsets in slots_per_tile slots
+ * (clamped to the tile length) instead of the default min(2 k_leaf + 64, T),
+ * or 0 slots above 12 GB of slots.  A tile with more kept pairs than slots is
+ * walked a second time by the emit pass; slots_per_tile = 0 walks every tile
+ * twice, as the default does for instances whose slots would pass 12 GB;
+ * negative keeps the default.  The output is the same bytes whatever the
+ * slot count.  slots_per_tile <= 2^20, else KG_ERR_ARG. */
+kg_status kg_gnp_ex_slots(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
+                          uint32_t k_leaf, int32_t slots_per_tile, int id_bytes, void* d_out,
+                          uint64_t cap_edges, uint64_t* d_count, void* stream);
+
 /*
  * G(n,p) by binomial chunk counts, Sec. 4.3: the sample count of every chunk
  * is a binomial variate Binomial(U_c, p) drawn from the stream of (seed, chunk
@@ -185,9 +197,14 @@ kg_status kg_gnp_binomial_count(int undirected, uint64_t n, double p, uint64_t s
  * Output: the same bytes as kg_gnm_directed with the same arguments.
  * Scratch: one array of KG_NOALLOC_SCRATCH_BYTES bytes compiled into the
  * library as a file-scope __device__ variable; every GPU that loads the
- * library holds it until the process exits.  Instances whose scratch would
- * not fit are rejected with KG_ERR_RANGE before any work is enqueued (about
- * a million tiles, i.e. m up to roughly 10^9 with the default leaf size).
+ * library holds it until the process exits.  An instance needs about 128
+ * bytes per tile (tiles = chunks * 2^d, d the tile-tree depth: the smallest d
+ * with m * ceil(n/chunks) / n <= 1024 * 2^d), plus a few KB: up to about 2^18
+ * tiles, i.e. m up to about 2.7 * 10^8 at the default leaf size.  The need is
+ * computed by the same code that carves the array (and reported by
+ * kg_gnm_directed_noalloc_scratch); an instance that does not fit is
+ * rejected with KG_ERR_RANGE before any work is enqueued, and d_status is
+ * then left untouched.
  * The call itself makes no cudaMalloc / cudaFree / pool allocation.
  * Set-up: the first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current and caches it; make that
@@ -206,6 +223,11 @@ kg_status kg_gnp_binomial_count(int undirected, uint64_t n, double p, uint64_t s
 kg_status kg_gnm_directed_noalloc(uint64_t n, uint64_t m, uint64_t seed, uint32_t chunks,
                                   int id_bytes, void* d_out, uint64_t cap_edges, int* d_status,
                                   void* stream);
+/* Bytes of the fixed array kg_gnm_directed_noalloc would use for (n, m,
+ * chunks), to *h_bytes (host memory); host-only, touches no device.  The call
+ * fits when the result is <= KG_NOALLOC_SCRATCH_BYTES. */
+kg_status kg_gnm_directed_noalloc_scratch(uint64_t n, uint64_t m, uint32_t chunks,
+                                          uint64_t* h_bytes);
 
 /*
  * Batched G(n,m): many independent instances generated together (the paper
@@ -358,6 +380,18 @@ kg_status kg_shutdown(void);
  */
 #define KG_PROF_CLASSES 9
 unsigned long long kg_launch_count(void);
+/* Ceilings measured with the library's own kernels (the caller times them,
+ * e.g. with CUDA events on `stream`):
+ * kg_peak_store writes `bytes` (a multiple of 16; d_buf 16-byte aligned) with
+ * 16-byte stores, evict-first (mode 0) or write-back (mode 1), in a grid of
+ * 8 blocks of 256 threads per SM -- the write-only bandwidth that bounds edge
+ * emission.  kg_peak_fp64 runs `blocks` blocks of 256 threads, each thread
+ * `iters` iterations of 8 independent chains x = x*a + b with separately
+ * rounded multiply and add (16 FP64 operations per iteration and thread) --
+ * the FP64 add/multiply rate that bounds the G(n,p) skip walk; d_out (2
+ * doubles) receives a checksum. */
+kg_status kg_peak_store(void* d_buf, uint64_t bytes, int mode, void* stream);
+kg_status kg_peak_fp64(double* d_out, uint32_t blocks, uint32_t iters, void* stream);
 kg_status kg_profile_begin(void);
 kg_status kg_profile_end(double* ms, unsigned long long* launches);
 

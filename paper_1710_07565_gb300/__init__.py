@@ -74,6 +74,10 @@ def lib() -> ctypes.CDLL:
                 "kg_rgg_grid": [i32, u64, dbl, ctypes.POINTER(ctypes.c_int)],
                 "kg_shutdown": [],
                 "kg_gnm_directed_noalloc": [u64, u64, u64, u32, i32, vp, u64, vp, vp],
+                "kg_gnm_directed_noalloc_scratch": [u64, u64, u32, ctypes.POINTER(u64)],
+                "kg_gnp_ex_slots": [i32, u64, dbl, u64, u32, u32, i32, i32, vp, u64, vp, vp],
+                "kg_peak_store": [vp, u64, i32, vp],
+                "kg_peak_fp64": [vp, u32, u32, vp],
             }
             for name, args in sigs.items():
                 f = getattr(L, name, None)
@@ -187,6 +191,14 @@ def kg_gnp_ex(undirected, n, p, seed, chunks, k_leaf, id_bytes, d_out, cap_edges
                  cap_edges, d_count, stream)
 
 
+def kg_gnp_ex_slots(undirected, n, p, seed, chunks, k_leaf, slots_per_tile, id_bytes, d_out,
+                    cap_edges, d_count, stream):
+    """kg_gnp_ex with the per-tile slot count set (a test hook: 0 walks every
+    tile twice, a small count makes tiles overflow their slots)."""
+    return _call("kg_gnp_ex_slots", int(undirected), n, p, seed, chunks, k_leaf, slots_per_tile,
+                 id_bytes, d_out, cap_edges, d_count, stream)
+
+
 def kg_gnm_undirected_chunk_counts(n, m, seed, chunks, d_counts, stream):
     return _call("kg_gnm_undirected_chunk_counts", n, m, seed, chunks, d_counts, stream)
 
@@ -211,6 +223,25 @@ def kg_gnm_directed_noalloc(n, m, seed, chunks, id_bytes, d_out, cap_edges, d_st
     the library (see include/kg.h for the size limit and the sharing rules)."""
     return _call("kg_gnm_directed_noalloc", n, m, seed, chunks, id_bytes, d_out, cap_edges,
                  d_status, stream)
+
+
+def kg_gnm_directed_noalloc_scratch(n, m, chunks) -> int:
+    """Bytes of the library's fixed array that kg_gnm_directed_noalloc would
+    use for (n, m, chunks) (host only)."""
+    b = ctypes.c_uint64(0)
+    _call("kg_gnm_directed_noalloc_scratch", n, m, chunks, ctypes.byref(b))
+    return b.value
+
+
+NOALLOC_SCRATCH_BYTES = 32 << 20  # KG_NOALLOC_SCRATCH_BYTES of include/kg.h
+
+
+def kg_peak_store(d_buf, nbytes, mode, stream):
+    return _call("kg_peak_store", d_buf, nbytes, mode, stream)
+
+
+def kg_peak_fp64(d_out, blocks, iters, stream):
+    return _call("kg_peak_fp64", d_out, blocks, iters, stream)
 
 
 def kg_edge_digest(d_edges, count, id_bytes, d_digest, stream):
@@ -455,8 +486,10 @@ def gnm_undirected(n, m, seed=1, chunks=1, id_bytes=4, k_leaf=K_LEAF_DEFAULT, k_
 
 
 def gnp(undirected, n, p, seed=1, chunks=1, id_bytes=4, k_leaf=K_LEAF_DEFAULT, cap=None,
-        stream=None, device="cuda"):
-    """G(n,p) edge list; returns (edges tensor view, device count tensor)."""
+        stream=None, device="cuda", slots_per_tile=-1):
+    """G(n,p) edge list; returns (edges tensor view, device count tensor).
+    slots_per_tile >= 0 sets the skip walk's per-tile slot count
+    (kg_gnp_ex_slots); the output does not depend on it."""
     import torch
     if cap is None:
         pairs = n * (n - 1) // (2 if undirected else 1)
@@ -464,8 +497,8 @@ def gnp(undirected, n, p, seed=1, chunks=1, id_bytes=4, k_leaf=K_LEAF_DEFAULT, c
         cap = int(min(pairs, mean + 12 * (mean ** 0.5) + 64)) * (2 if undirected else 1)
     out = _empty_edges(cap, id_bytes, device)
     cnt = torch.zeros(1, dtype=torch.int64, device=device)
-    kg_gnp_ex(undirected, n, p, seed, chunks, k_leaf, id_bytes, out.data_ptr(), cap, cnt.data_ptr(),
-              _stream_ptr(stream))
+    kg_gnp_ex_slots(undirected, n, p, seed, chunks, k_leaf, slots_per_tile, id_bytes,
+                    out.data_ptr(), cap, cnt.data_ptr(), _stream_ptr(stream))
     return out, cnt
 
 

@@ -34,6 +34,21 @@ int* device_error_word() {
   return p;
 }
 
+int sm_count() {
+  static std::mutex mu;
+  static std::unordered_map<int, int> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+    n = 152;
+  cache[dev] = n;
+  return n;
+}
+
 // ---------------------------------------------------------------- directed
 struct DirParams {
   uint64_t n, m;
@@ -68,10 +83,11 @@ static int check_directed(uint64_t n, uint64_t m, uint32_t P, uint32_t k_leaf, u
 static DirGeom dir_geom(uint64_t n, uint32_t P) { return DirGeom::make(n, P); }
 
 // Chunk split tree: bands of 8 levels, one block per subtree root.
-static int run_chunk_tree(const DirParams& dp, uint64_t seed, uint64_t* cnt, Workspace& ws,
+// node_cnt: scratch of 2^(D+1) counts (chunk_tree_nodes).
+static uint64_t chunk_tree_nodes(const DirParams& dp) { return uint64_t(2) << dp.D; }
+
+static int run_chunk_tree(const DirParams& dp, uint64_t seed, uint64_t* cnt, uint64_t* node_cnt,
                           cudaStream_t s, int* err) {
-  uint64_t* node_cnt = ws.alloc<uint64_t>(uint64_t(2) << dp.D);
-  if (!ws.ok()) return ST_CUDA;
   for (int l0 = 0; l0 <= dp.D; l0 += 8) {
     const int l1 = (l0 + 8 < dp.D + 1) ? l0 + 8 : dp.D + 1;
     ProfScope ps(PROF_CHUNK_TREE, s);
@@ -80,6 +96,35 @@ static int run_chunk_tree(const DirParams& dp, uint64_t seed, uint64_t* cnt, Wor
     if (launch_ok()) return ST_CUDA;
   }
   return ST_OK;
+}
+
+static int run_chunk_tree(const DirParams& dp, uint64_t seed, uint64_t* cnt, Workspace& ws,
+                          cudaStream_t s, int* err) {
+  uint64_t* node_cnt = ws.alloc<uint64_t>(chunk_tree_nodes(dp));
+  if (!ws.ok()) return ST_CUDA;
+  return run_chunk_tree(dp, seed, cnt, node_cnt, s, err);
+}
+
+// Everything a whole directed instance takes from scratch, carved in one
+// place: the chunk counts, the chunk-tree nodes and the run over all chunks.
+struct DirectedScratch {
+  uint64_t* cnt = nullptr;
+  uint64_t* node_cnt = nullptr;
+  ChunkRunScratch<DirGeom::Ctx> run;
+  bool carve(const DirParams& dp, Workspace& ws) {
+    cnt = ws.alloc<uint64_t>(dp.P);
+    node_cnt = ws.alloc<uint64_t>(chunk_tree_nodes(dp));
+    return run.carve(dp.P, dp.d, false, false, false, ws) && ws.ok();
+  }
+};
+
+// Bytes of scratch a whole directed instance takes (a measuring pass of the
+// same carve that the run uses).
+static uint64_t directed_scratch_bytes(const DirParams& dp) {
+  Workspace meas = Workspace::measuring();
+  DirectedScratch sc;
+  if (!sc.carve(dp, meas)) return ~uint64_t(0);
+  return meas.used();
 }
 
 }  // namespace kg
@@ -159,12 +204,12 @@ kg_status kg_gnm_directed_ex(uint64_t n, uint64_t m, uint64_t seed, uint32_t chu
   if (!err) return KG_ERR_CUDA;
   cudaStream_t s = as_stream(stream);
   Workspace ws(s);
-  uint64_t* cnt = ws.alloc<uint64_t>(chunks);
-  if (!ws.ok()) return KG_ERR_CUDA;
-  st = run_chunk_tree(dp, seed, cnt, ws, s, err);
+  DirectedScratch sc;
+  if (!sc.carve(dp, ws)) return KG_ERR_CUDA;
+  st = run_chunk_tree(dp, seed, sc.cnt, sc.node_cnt, s, err);
   if (st) return kg_status(st);
-  st = run_chunks(dir_geom(n, chunks), 0, chunks, cnt, dp.d, k_max, seed, id_bytes, d_out,
-                  cap_edges, ws, s, err);
+  st = run_chunks_carved(dir_geom(n, chunks), 0, chunks, sc.cnt, dp.d, k_max, seed, id_bytes,
+                         d_out, cap_edges, sc.run, s, err, nullptr, nullptr);
   return kg_status(st);
 }
 
@@ -227,26 +272,6 @@ void* noalloc_scratch_address() {
   return p;
 }
 
-uint64_t piece(uint64_t bytes) { return (bytes + 255) & ~uint64_t(255); }
-
-// Scratch bytes the directed orchestration takes, in its allocation order.
-uint64_t scan_bytes(uint64_t n) {
-  const uint64_t items = 512 * 8;
-  const uint64_t nb = (n + items - 1) / items;
-  if (n == 0 || nb == 1) return 0;
-  return piece(nb * 8) + piece((nb + 1) * 8) + scan_bytes(nb);
-}
-uint64_t directed_scratch_bytes(const DirParams& dp) {
-  const uint64_t P = dp.P, T = P << dp.d;
-  uint64_t b = piece(P * 8);                       // chunk counts
-  b += piece((uint64_t(2) << dp.D) * 8);           // chunk-tree node counts
-  if (dp.d > 0) b += 2 * piece(T * 8);             // tile-tree levels (ping-pong)
-  b += piece((T + 1) * 8);                         // tile offsets
-  b += scan_bytes(T);                              // scan partials
-  b += piece(T * 8) + piece(8);                    // over-full tile list + its length
-  return b;
-}
-
 }  // namespace
 }  // namespace kg
 
@@ -258,22 +283,35 @@ extern "C" kg_status kg_gnm_directed_noalloc(uint64_t n, uint64_t m, uint64_t se
   if (st) return kg_status(st);
   if (!d_status) return KG_ERR_ARG;
   if (cap_edges < m) return KG_ERR_CAPACITY;
+  // the same carve, measured: an instance whose scratch does not fit is
+  // rejected here, before anything is enqueued
   if (directed_scratch_bytes(dp) > uint64_t(KG_NOALLOC_SCRATCH_BYTES)) return KG_ERR_RANGE;
   if (m > 0 && !d_out) return KG_ERR_ARG;
   void* arena = noalloc_scratch_address();
   if (!arena) return KG_ERR_CUDA;
   cudaStream_t s = as_stream(stream);
+  Workspace ws(s, arena, KG_NOALLOC_SCRATCH_BYTES);
+  DirectedScratch sc;
+  if (!sc.carve(dp, ws)) return KG_ERR_INTERNAL;  // cannot happen after the check above
   // device-side checks report into the caller's status word, cleared first
   int* err = d_status;
   if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return KG_ERR_CUDA;
   if (m == 0) return KG_OK;
-  Workspace ws(s, arena, KG_NOALLOC_SCRATCH_BYTES);
-  uint64_t* cnt = ws.alloc<uint64_t>(chunks);
-  if (!ws.ok()) return KG_ERR_INTERNAL;
-  st = run_chunk_tree(dp, seed, cnt, ws, s, err);
+  st = run_chunk_tree(dp, seed, sc.cnt, sc.node_cnt, s, err);
   if (st) return kg_status(st);
-  st = run_chunks(dir_geom(n, chunks), 0, chunks, cnt, dp.d, K_MAX, seed, id_bytes, d_out,
-                  cap_edges, ws, s, err);
+  st = run_chunks_carved(dir_geom(n, chunks), 0, chunks, sc.cnt, dp.d, K_MAX, seed, id_bytes,
+                         d_out, cap_edges, sc.run, s, err, nullptr, nullptr);
+  return kg_status(st);
+}
+
+// Scratch bytes kg_gnm_directed_noalloc needs for an instance (host only, no
+// device work): what its arena check compares with KG_NOALLOC_SCRATCH_BYTES.
+extern "C" kg_status kg_gnm_directed_noalloc_scratch(uint64_t n, uint64_t m, uint32_t chunks,
+                                                     uint64_t* h_bytes) {
+  DirParams dp;
+  int st = check_directed(n, m, chunks, K_LEAF, K_MAX, 8, dp);
   if (st) return kg_status(st);
-  return ws.ok() ? KG_OK : KG_ERR_INTERNAL;
+  if (!h_bytes) return KG_ERR_ARG;
+  *h_bytes = directed_scratch_bytes(dp);
+  return KG_OK;
 }

@@ -64,7 +64,7 @@ static int run_quadtree(const UndParams& up, uint64_t seed, uint64_t* chunk_cnt,
     const uint64_t bound = (l < 16) ? ((uint64_t(1) << l) * ((uint64_t(1) << l) + 1) / 2) : C;
     ProfScope ps(PROF_CHUNK_TREE, s);
     // one-warp blocks spread the few FP64-bound nodes of the top levels over the SMs
-    quad_level<<<grid_for(bound < C ? bound : C, 32, 152 * 64), 32, 0, s>>>(
+    quad_level<<<grid_for(bound < C ? bound : C, 32, sm_count() * 64), 32, 0, s>>>(
         rb, seed, (l & 1) ? L1 : L0, counts + l, (l & 1) ? L0 : L1, counts + l + 1, chunk_cnt, err);
     if (launch_ok()) return ST_CUDA;
   }
@@ -155,7 +155,7 @@ static int gnm_undirected_rows_impl(const UndParams& up, uint64_t seed, uint32_t
     return ST_CUDA;
   {
     ProfScope ps(PROF_OTHER, s);
-    gather_counts<<<grid_for(L, 256, 152 * 8), 256, 0, s>>>(d_counts, dlist, L, cnt);
+    gather_counts<<<grid_for(L, 256, sm_count() * 8), 256, 0, s>>>(d_counts, dlist, L, cnt);
     if (launch_ok()) return ST_CUDA;
   }
   if ((st = scan_exclusive_u64(cnt, off, L, ws, s))) return st;
@@ -183,7 +183,7 @@ static int gnm_undirected_rows_impl(const UndParams& up, uint64_t seed, uint32_t
         (d_hist && cudaMemsetAsync(d_hist, 0, nb * 65 * 8, s) != cudaSuccess))
       return ST_CUDA;
     ProfScope ps(PROF_DIGEST, s);
-    und_block_digest<Id><<<grid_for(nrows, unsigned(DIGEST_SEG), 152 * 16), 256, 0, s>>>(
+    und_block_digest<Id><<<grid_for(nrows, unsigned(DIGEST_SEG), sm_count() * 16), 256, 0, s>>>(
         out, rowptr, row_lo, nrows, rb, b0, reinterpret_cast<unsigned long long*>(d_digest),
         reinterpret_cast<unsigned long long*>(d_hist));
     if (launch_ok()) return ST_CUDA;
@@ -236,7 +236,7 @@ static int gnp_impl(const Geom& g, uint64_t C, bool undirected, uint64_t n, cons
   if (!undirected) {
     PairSink<Id> sink{static_cast<Id*>(d_out), cap, err};
     ProfScope ps(PROF_LEAF, s);
-    gnp_emit<Geom, SlotT, PairSink<Id>><<<grid_for(tiles, 4, 152 * 64), 128, 0, s>>>(
+    gnp_emit<Geom, SlotT, PairSink<Id>><<<grid_for(tiles, 4, sm_count() * 64), 128, 0, s>>>(
         g, pl, seed, C, slots, cnt, off, sink);
     return launch_ok();
   }
@@ -248,7 +248,7 @@ static int gnp_impl(const Geom& g, uint64_t C, bool undirected, uint64_t n, cons
     // check above already recorded the capacity error
     PairSink<Id> sink{pairs, pcap, nullptr};
     ProfScope ps(PROF_LEAF, s);
-    gnp_emit<Geom, SlotT, PairSink<Id>><<<grid_for(tiles, 4, 152 * 64), 128, 0, s>>>(
+    gnp_emit<Geom, SlotT, PairSink<Id>><<<grid_for(tiles, 4, sm_count() * 64), 128, 0, s>>>(
         g, pl, seed, C, slots, cnt, off, sink);
     if (launch_ok()) return ST_CUDA;
   }
@@ -322,7 +322,7 @@ static int gnpb_counts(const Geom& g, uint64_t C, double p, uint64_t seed, uint6
                        cudaStream_t s, int* err) {
   ProfScope ps(PROF_CHUNK_TREE, s);
   // one-warp blocks: a few hundred FP64 binomials spread over the SMs
-  gnp_chunk_counts<Geom><<<grid_for(C, 32, 152 * 64), 32, 0, s>>>(g, C, p, seed, cnt, err);
+  gnp_chunk_counts<Geom><<<grid_for(C, 32, sm_count() * 64), 32, 0, s>>>(g, C, p, seed, cnt, err);
   return launch_ok();
 }
 
@@ -425,8 +425,10 @@ kg_status kg_gnm_undirected(uint64_t n, uint64_t m, uint64_t seed, uint32_t chun
 }
 
 // Validation and tile plan shared by kg_gnp_ex and kg_gnp_count.
+// slots_per_tile >= 0 replaces the slot count of a tile (clamped to the tile
+// length); negative keeps the default.
 static int gnp_prepare(int undirected, uint64_t n, double p, uint32_t chunks, uint32_t k_leaf,
-                       int id_bytes, GnpPlan& pl, uint64_t& C) {
+                       int id_bytes, GnpPlan& pl, uint64_t& C, int64_t slots_per_tile = -1) {
   if (!(p >= 0.0 && p <= 1.0) || k_leaf < 2) return ST_ARG;
   if (n == 0 || chunks == 0 || uint64_t(chunks) > n) return ST_ARG;
   if (id_bytes != 4 && id_bytes != 8) return ST_ARG;
@@ -456,17 +458,20 @@ static int gnp_prepare(int undirected, uint64_t n, double p, uint32_t chunks, ui
   const uint64_t slot_bytes = (pl.T <= (uint64_t(1) << 32)) ? 4 : 8;
   // slots above this size: tiles are walked a second time instead
   if (uint64_t(tiles) * cap_t * slot_bytes > (uint64_t(12) << 30)) cap_t = 0;
+  if (slots_per_tile >= 0 && !pl.all)
+    cap_t = uint64_t(slots_per_tile) < pl.T ? uint64_t(slots_per_tile) : pl.T;
   pl.cap_t = uint32_t(cap_t);
   return ST_OK;
 }
 
-kg_status kg_gnp_ex(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
-                    uint32_t k_leaf, int id_bytes, void* d_out, uint64_t cap_edges,
-                    uint64_t* d_count, void* stream) {
+kg_status kg_gnp_ex_slots(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
+                          uint32_t k_leaf, int32_t slots_per_tile, int id_bytes, void* d_out,
+                          uint64_t cap_edges, uint64_t* d_count, void* stream) {
   if (!d_count) return KG_ERR_ARG;
+  if (slots_per_tile > (int32_t(1) << 20)) return KG_ERR_ARG;
   GnpPlan pl;
   uint64_t C = 0;
-  int st = gnp_prepare(undirected, n, p, chunks, k_leaf, id_bytes, pl, C);
+  int st = gnp_prepare(undirected, n, p, chunks, k_leaf, id_bytes, pl, C, slots_per_tile);
   if (st) return kg_status(st);
   cudaStream_t s = as_stream(stream);
   if (cudaMemsetAsync(d_count, 0, sizeof(uint64_t), s) != cudaSuccess) return KG_ERR_CUDA;
@@ -486,6 +491,13 @@ kg_status kg_gnp_ex(int undirected, uint64_t n, double p, uint64_t seed, uint32_
              : gnp_dispatch_slots<DirGeom, uint64_t>(g, C, false, n, pl, seed, d_out, cap_edges, d_count, s, err);
   }
   return kg_status(st);
+}
+
+kg_status kg_gnp_ex(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,
+                    uint32_t k_leaf, int id_bytes, void* d_out, uint64_t cap_edges,
+                    uint64_t* d_count, void* stream) {
+  return kg_gnp_ex_slots(undirected, n, p, seed, chunks, k_leaf, -1, id_bytes, d_out, cap_edges,
+                         d_count, stream);
 }
 
 kg_status kg_gnp_count(int undirected, uint64_t n, double p, uint64_t seed, uint32_t chunks,

@@ -30,7 +30,7 @@ inline int assemble(const Id* pairs, const uint64_t* npairs_dev, uint64_t npairs
   const uint64_t work = work_bound ? work_bound : (npairs_dev ? cap / 2 : npairs_host);
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    und_degree<Id><<<grid_for(work, 256, 152 * 16), 256, 0, s>>>(pairs, npairs_dev, npairs_host,
+    und_degree<Id><<<grid_for(work, 256, sm_count() * 16), 256, 0, s>>>(pairs, npairs_dev, npairs_host,
                                                                  row_lo, nrows, deg);
     if (launch_ok()) return ST_CUDA;
   }
@@ -40,18 +40,18 @@ inline int assemble(const Id* pairs, const uint64_t* npairs_dev, uint64_t npairs
     return ST_CUDA;
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    und_scatter<Id><<<grid_for(work, 256, 152 * 16), 256, 0, s>>>(
+    und_scatter<Id><<<grid_for(work, 256, sm_count() * 16), 256, 0, s>>>(
         pairs, npairs_dev, npairs_host, row_lo, nrows, cursor, out, cap, err);
     if (launch_ok()) return ST_CUDA;
   }
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    und_sort_short<Id><<<grid_for(nrows, 256, 152 * 32), 256, 0, s>>>(rowptr, nrows, out, cap,
+    und_sort_short<Id><<<grid_for(nrows, 256, sm_count() * 32), 256, 0, s>>>(rowptr, nrows, out, cap,
                                                                     long_rows, nlong);
     if (launch_ok()) return ST_CUDA;
   }
   ProfScope ps(PROF_ASSEMBLY, s);
-  und_sort_long<Id><<<152 * 2, 256, 0, s>>>(rowptr, out, cap, long_rows, nlong);
+  und_sort_long<Id><<<sm_count() * 2, 256, 0, s>>>(rowptr, out, cap, long_rows, nlong);
   return launch_ok();
 }
 

@@ -554,7 +554,7 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
   if (cudaMemsetAsync(bp->nbig, 0, 8, s) != cudaSuccess) return ST_CUDA;
   {
     ProfScope ps(PROF_OTHER, s);
-    batch_desc<<<grid_for(bp->tiles, 256, 152 * 32), 256, 0, s>>>(
+    batch_desc<<<grid_for(bp->tiles, 256, sm_count() * 32), 256, 0, s>>>(
         bp->inst, count, bp->tiles, K_MAX, bp->tile_cnt, bp->tile_off, bp->desc, bp->big,
         bp->nbig, err);
     if (launch_ok()) return ST_CUDA;
@@ -570,7 +570,7 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
   }
   {
     ProfScope ps(PROF_OTHER, s);
-    leaf_resplit_kernel<BatchGeom, BatchSink, false, TileDesc<BatchCtx>><<<152, LEAF_THREADS, 0, s>>>(
+    leaf_resplit_kernel<BatchGeom, BatchSink, false, TileDesc<BatchCtx>><<<sm_count(), LEAF_THREADS, 0, s>>>(
         BatchGeom{}, sink, K_MAX, bp->desc, err, DigestOut{nullptr, nullptr, nullptr}, bp->big,
         bp->nbig);
     if (launch_ok()) return ST_CUDA;
@@ -582,7 +582,7 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
     return ST_CUDA;
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    batch_und_degree<<<grid_for(Mp, 256, 152 * 32), 256, 0, s>>>(bp->inst, count, Mp,
+    batch_und_degree<<<grid_for(Mp, 256, sm_count() * 32), 256, 0, s>>>(bp->inst, count, Mp,
                                                                  bp->pairs_buf, bp->deg);
     if (launch_ok()) return ST_CUDA;
   }
@@ -590,7 +590,7 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
   if (st) return st;
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    batch_und_rowpos<<<grid_for(V, 256, 152 * 32), 256, 0, s>>>(bp->inst, count, V, bp->rowptr,
+    batch_und_rowpos<<<grid_for(V, 256, sm_count() * 32), 256, 0, s>>>(bp->inst, count, V, bp->rowptr,
                                                                 bp->rowpos);
     if (launch_ok()) return ST_CUDA;
   }
@@ -598,20 +598,20 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
     return ST_CUDA;
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    batch_und_scatter<<<grid_for(Mp, 256, 152 * 32), 256, 0, s>>>(bp->inst, count, Mp,
+    batch_und_scatter<<<grid_for(Mp, 256, sm_count() * 32), 256, 0, s>>>(bp->inst, count, Mp,
                                                                   bp->pairs_buf, bp->cursor, out,
                                                                   cap, err);
     if (launch_ok()) return ST_CUDA;
   }
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    batch_und_sort_short<<<grid_for(V, 256, 152 * 32), 256, 0, s>>>(V, bp->rowpos, bp->deg, out, cap,
+    batch_und_sort_short<<<grid_for(V, 256, sm_count() * 32), 256, 0, s>>>(V, bp->rowpos, bp->deg, out, cap,
                                                                   bp->long_rows, bp->nlong);
     if (launch_ok()) return ST_CUDA;
   }
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    batch_und_sort_long<<<152 * 2, 256, 0, s>>>(bp->rowpos, bp->deg, out, bp->long_rows,
+    batch_und_sort_long<<<sm_count() * 2, 256, 0, s>>>(bp->rowpos, bp->deg, out, bp->long_rows,
                                                 bp->nlong);
     if (launch_ok()) return ST_CUDA;
   }
@@ -806,7 +806,7 @@ kg_status kg_batch_tune(kg_batch* b, void* d_out, uint64_t cap_entries, int reps
   if (b->plan.count == 0 || b->plan.entries == 0) return KG_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const unsigned trees[] = {128, 256};
-  const unsigned grids[] = {0x7fffffffu, 152u * 5 * 8, 152u * 5 * 2};
+  const unsigned grids[] = {0x7fffffffu, unsigned(sm_count()) * 5 * 8, unsigned(sm_count()) * 5 * 2};
   float best = 1e30f;
   unsigned bt = 256, bg = 0x7fffffffu;
   cudaEvent_t e0, e1;

@@ -41,7 +41,7 @@ inline int edge_digest(const void* e, uint64_t count, int id_bytes, uint64_t* ou
   if (cudaMemsetAsync(out, 0, sizeof(uint64_t), s) != cudaSuccess) return ST_CUDA;
   if (count == 0) return ST_OK;
   uint64_t blocks = (count + 255) / 256;
-  if (blocks > 152 * 32) blocks = 152 * 32;
+  if (blocks > sm_count() * 32) blocks = sm_count() * 32;
   ProfScope ps(PROF_DIGEST, s);
   if (id_bytes == 4)
     edge_digest_kernel<uint32_t><<<unsigned(blocks), 256, 0, s>>>(

@@ -268,13 +268,13 @@ int rgg_run(const RggGrid& G, uint64_t seed, RggStop stop, int id_bytes, void* d
   if (!ws.ok()) return ST_CUDA;
   for (int level = 0; level < D; ++level) {
     ProfScope ps(PROF_RGG, s);
-    rgg_tree_level<<<grid_for(uint64_t(1) << level, 256, 152 * 16), 256, 0, s>>>(cz, D, level,
+    rgg_tree_level<<<grid_for(uint64_t(1) << level, 256, sm_count() * 16), 256, 0, s>>>(cz, D, level,
                                                                                  n, seed, err);
     if (launch_ok()) return ST_CUDA;
   }
   {
     ProfScope ps(PROF_RGG, s);
-    rgg_rowmajor<DIM><<<grid_for(G.cells, 256, 152 * 16), 256, 0, s>>>(cz, G.g, n, cq);
+    rgg_rowmajor<DIM><<<grid_for(G.cells, 256, sm_count() * 16), 256, 0, s>>>(cz, G.g, n, cq);
     if (launch_ok()) return ST_CUDA;
   }
   if (stop == RggStop::CELLS) return ST_OK;
@@ -288,11 +288,11 @@ int rgg_run(const RggGrid& G, uint64_t seed, RggStop stop, int id_bytes, void* d
   if (st) return st;
   {
     ProfScope ps(PROF_RGG, s);
-    rgg_points<DIM><<<grid_for(G.cells, RGG_CELLS_PER_BLOCK, 152 * 8), 256, 0, s>>>(
+    rgg_points<DIM><<<grid_for(G.cells, RGG_CELLS_PER_BLOCK, sm_count() * 8), 256, 0, s>>>(
         S, G.g, seed, P, d_coords);
     if (launch_ok()) return ST_CUDA;
   }
-  const unsigned eblocks = grid_for(n, 256, 152 * 16);
+  const unsigned eblocks = grid_for(n, 256, sm_count() * 16);
   {
     ProfScope ps(PROF_RGG, s);
     rgg_edges<DIM, false, uint32_t><<<eblocks, 256, 0, s>>>(P, uint32_t(n), G.g, uint32_t(G.R), S,

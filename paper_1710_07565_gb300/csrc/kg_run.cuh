@@ -36,24 +36,55 @@ inline unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
 
 inline int launch_ok() { return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA; }
 
-// Tile trees + scan + leaves for chunks [c_begin, c_begin + C) of a geometry.
-// level0: the chunks' counts (device).  Pairs go to d_out[0 ..).  With digest
-// pointers the leaf kernel also produces the per-chunk digest and out-degree
-// histogram (directed geometry only).
+// Scratch of one run_chunks call, carved by one function before any launch,
+// so that a measuring Workspace counts exactly the bytes a run takes.
+template <class Ctx>
+struct ChunkRunScratch {
+  uint64_t *A = nullptr, *B = nullptr;  // tile-tree levels (ping-pong)
+  uint64_t* tile_off = nullptr;         // T + 1 scanned tile counts
+  ScanScratch scan;
+  unsigned long long* digest = nullptr;  // per chunk, when the caller gives none
+  unsigned long long* hist = nullptr;    // per chunk x 65, likewise
+  TileRec* rec = nullptr;                // per tile run records
+  unsigned long long *big = nullptr, *nbig = nullptr;  // tiles over k_max
+  TileDesc<Ctx>* desc = nullptr;         // per tile descriptors
+
+  // C chunks with tile depth d; digest / hist: whether the caller gives them;
+  // want: whether the digest and histogram are produced at all.
+  bool carve(uint64_t C, int d, bool want, bool have_digest, bool have_hist, Workspace& ws) {
+    const uint64_t T = C << d;
+    if (d > 0) {
+      A = ws.alloc<uint64_t>(T);
+      B = ws.alloc<uint64_t>(T);
+    }
+    tile_off = ws.alloc<uint64_t>(T + 1);
+    if (!scan_scratch(T, ws, scan)) return false;
+    if (want) {
+      if (!have_digest) digest = ws.alloc<unsigned long long>(C);
+      if (!have_hist) hist = ws.alloc<unsigned long long>(C * 65);
+      rec = ws.alloc<TileRec>(T);
+    }
+    big = ws.alloc<unsigned long long>(T);
+    nbig = ws.alloc<unsigned long long>(1);
+    desc = ws.alloc<TileDesc<Ctx>>(T);
+    return ws.ok();
+  }
+};
+
+// Tile descriptors + leaf kernels over the T tiles of a run.
 template <class Geom, class Sink, bool DIGEST>
 inline int launch_leaf(const Geom& g, const Sink& sink, uint64_t c_begin, int d, uint32_t k_max,
                        uint64_t seed, const uint64_t* tile_cnt, const uint64_t* tile_off,
-                       uint64_t T, int* err, DigestOut dig, Workspace& ws, cudaStream_t s) {
-  unsigned long long* big = ws.alloc<unsigned long long>(T);
-  unsigned long long* nbig = ws.alloc<unsigned long long>(1);
-  if (!ws.ok()) return ST_CUDA;
+                       uint64_t T, int* err, DigestOut dig,
+                       const ChunkRunScratch<typename Geom::Ctx>& sc, cudaStream_t s) {
+  unsigned long long* big = sc.big;
+  unsigned long long* nbig = sc.nbig;
   if (cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), s) != cudaSuccess) return ST_CUDA;
   using Desc = TileDesc<typename Geom::Ctx>;
-  Desc* desc = ws.alloc<Desc>(T);
-  if (!ws.ok()) return ST_CUDA;
+  Desc* desc = sc.desc;
   {
     ProfScope ps(PROF_OTHER, s);
-    tile_desc_kernel<Geom><<<grid_for(T, 256, 152 * 32), 256, 0, s>>>(
+    tile_desc_kernel<Geom><<<grid_for(T, 256, sm_count() * 32), 256, 0, s>>>(
         g, c_begin, d, k_max, seed, tile_cnt, tile_off, T, desc, big, nbig, err);
     if (launch_ok()) return ST_CUDA;
   }
@@ -65,45 +96,43 @@ inline int launch_leaf(const Geom& g, const Sink& sink, uint64_t c_begin, int d,
     if (launch_ok()) return ST_CUDA;
   }
   ProfScope ps(PROF_OTHER, s);
-  leaf_resplit_kernel<Geom, Sink, DIGEST, Desc><<<152, LEAF_THREADS, 0, s>>>(
+  leaf_resplit_kernel<Geom, Sink, DIGEST, Desc><<<sm_count(), LEAF_THREADS, 0, s>>>(
       g, sink, k_max, desc, err, dig, big, nbig);
   return launch_ok();
 }
 
+// Tile trees + scan + leaves for chunks [c_begin, c_begin + C) of a geometry,
+// with scratch carved beforehand (ChunkRunScratch::carve with the same C, d
+// and digest arguments).  level0: the chunks' counts (device).  Pairs go to
+// d_out[0 ..).  With digest pointers the leaf kernel also produces the
+// per-chunk digest and out-degree histogram (directed geometry only).
 template <class Geom>
-int run_chunks(const Geom& g, uint64_t c_begin, uint64_t C, const uint64_t* level0, int d,
-               uint32_t k_max, uint64_t seed, int id_bytes, void* d_out, uint64_t cap,
-               Workspace& ws, cudaStream_t s, int* err, uint64_t* digest = nullptr,
-               uint64_t* hist = nullptr) {
+int run_chunks_carved(const Geom& g, uint64_t c_begin, uint64_t C, const uint64_t* level0, int d,
+                      uint32_t k_max, uint64_t seed, int id_bytes, void* d_out, uint64_t cap,
+                      const ChunkRunScratch<typename Geom::Ctx>& sc, cudaStream_t s, int* err,
+                      uint64_t* digest, uint64_t* hist) {
   const uint64_t T = C << d;
   const uint64_t* in = level0;
-  if (d > 0) {
-    uint64_t* A = ws.alloc<uint64_t>(T);
-    uint64_t* B = ws.alloc<uint64_t>(T);
-    if (!ws.ok()) return ST_CUDA;
-    for (int level = 0; level < d; ++level) {
-      uint64_t* out = (level & 1) ? B : A;
-      const uint64_t nodes = C << level;
-      ProfScope ps(PROF_TILE_TREE, s);
-      // one-warp blocks: the top levels hold a few thousand FP64-bound nodes,
-      // which 256-thread blocks would pile onto a few SMs
-      tile_tree_level<Geom><<<grid_for(nodes, 32, 152 * 64), 32, 0, s>>>(
-          g, c_begin, C, d, level, seed, in, out, err);
-      if (launch_ok()) return ST_CUDA;
-      in = out;
-    }
+  for (int level = 0; level < d; ++level) {
+    uint64_t* out = (level & 1) ? sc.B : sc.A;
+    const uint64_t nodes = C << level;
+    ProfScope ps(PROF_TILE_TREE, s);
+    // one-warp blocks: the top levels hold a few thousand FP64-bound nodes,
+    // which 256-thread blocks would pile onto a few SMs
+    tile_tree_level<Geom><<<grid_for(nodes, 32, sm_count() * 64), 32, 0, s>>>(g, c_begin, C, d, level,
+                                                                       seed, in, out, err);
+    if (launch_ok()) return ST_CUDA;
+    in = out;
   }
-  uint64_t* tile_off = ws.alloc<uint64_t>(T + 1);
-  if (!ws.ok()) return ST_CUDA;
-  int st = scan_exclusive_u64(in, tile_off, T, ws, s);
+  uint64_t* tile_off = sc.tile_off;
+  int st = scan_exclusive_u64(in, tile_off, T, sc.scan, s);
   if (st) return st;
   const bool want = digest || hist;
   DigestOut dig{nullptr, nullptr, nullptr};
   if (want) {
-    dig.digest = reinterpret_cast<unsigned long long*>(digest ? digest : ws.alloc<uint64_t>(C));
-    dig.hist = reinterpret_cast<unsigned long long*>(hist ? hist : ws.alloc<uint64_t>(C * 65));
-    dig.rec = ws.alloc<TileRec>(T);
-    if (!ws.ok()) return ST_CUDA;
+    dig.digest = digest ? reinterpret_cast<unsigned long long*>(digest) : sc.digest;
+    dig.hist = hist ? reinterpret_cast<unsigned long long*>(hist) : sc.hist;
+    dig.rec = sc.rec;
     if (cudaMemsetAsync(dig.digest, 0, C * sizeof(uint64_t), s) != cudaSuccess ||
         cudaMemsetAsync(dig.hist, 0, C * 65 * sizeof(uint64_t), s) != cudaSuccess ||
         cudaMemsetAsync(dig.rec, 0, T * sizeof(TileRec), s) != cudaSuccess)
@@ -112,21 +141,32 @@ int run_chunks(const Geom& g, uint64_t c_begin, uint64_t C, const uint64_t* leve
   if (id_bytes == 4) {
     PairSink<uint32_t> sink{static_cast<uint32_t*>(d_out), cap, err};
     st = want ? launch_leaf<Geom, PairSink<uint32_t>, true>(g, sink, c_begin, d, k_max, seed, in,
-                                                             tile_off, T, err, dig, ws, s)
+                                                             tile_off, T, err, dig, sc, s)
               : launch_leaf<Geom, PairSink<uint32_t>, false>(g, sink, c_begin, d, k_max, seed, in,
-                                                              tile_off, T, err, dig, ws, s);
+                                                              tile_off, T, err, dig, sc, s);
   } else {
     PairSink<uint64_t> sink{static_cast<uint64_t*>(d_out), cap, err};
     st = want ? launch_leaf<Geom, PairSink<uint64_t>, true>(g, sink, c_begin, d, k_max, seed, in,
-                                                             tile_off, T, err, dig, ws, s)
+                                                             tile_off, T, err, dig, sc, s)
               : launch_leaf<Geom, PairSink<uint64_t>, false>(g, sink, c_begin, d, k_max, seed, in,
-                                                              tile_off, T, err, dig, ws, s);
+                                                              tile_off, T, err, dig, sc, s);
   }
   if (st || !want) return st;
   ProfScope ps(PROF_DIGEST, s);
-  chunk_run_merge<Geom><<<grid_for(C, 128, 152 * 8), 128, 0, s>>>(g, c_begin, C, d, dig.rec,
+  chunk_run_merge<Geom><<<grid_for(C, 128, sm_count() * 8), 128, 0, s>>>(g, c_begin, C, d, dig.rec,
                                                                    dig.hist);
   return launch_ok();
+}
+
+template <class Geom>
+int run_chunks(const Geom& g, uint64_t c_begin, uint64_t C, const uint64_t* level0, int d,
+               uint32_t k_max, uint64_t seed, int id_bytes, void* d_out, uint64_t cap,
+               Workspace& ws, cudaStream_t s, int* err, uint64_t* digest = nullptr,
+               uint64_t* hist = nullptr) {
+  ChunkRunScratch<typename Geom::Ctx> sc;
+  if (!sc.carve(C, d, digest || hist, digest != nullptr, hist != nullptr, ws)) return ST_CUDA;
+  return run_chunks_carved(g, c_begin, C, level0, d, k_max, seed, id_bytes, d_out, cap, sc, s, err,
+                           digest, hist);
 }
 
 }  // namespace kg

@@ -51,8 +51,22 @@ __global__ void __launch_bounds__(SCAN_THREADS)
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) out[n] = run;
 }
 
-int scan_exclusive_u64(const uint64_t* in, uint64_t* out, uint64_t n, Workspace& ws,
-                       cudaStream_t s) {
+bool scan_scratch(uint64_t n, Workspace& ws, ScanScratch& sc) {
+  sc.levels = 0;
+  for (;;) {
+    if (n == 0) return ws.ok();
+    const uint64_t nb = (n + SCAN_ITEMS - 1) / SCAN_ITEMS;
+    if (nb == 1) return ws.ok();
+    if (sc.levels == ScanScratch::LEVELS) return false;
+    sc.part[sc.levels] = ws.alloc<uint64_t>(nb);
+    sc.carry[sc.levels] = ws.alloc<uint64_t>(nb + 1);
+    ++sc.levels;
+    n = nb;
+  }
+}
+
+static int scan_level(const uint64_t* in, uint64_t* out, uint64_t n, const ScanScratch& sc,
+                      int level, cudaStream_t s) {
   if (n == 0) {
     return cudaMemsetAsync(out, 0, sizeof(uint64_t), s) == cudaSuccess ? ST_OK : ST_CUDA;
   }
@@ -62,18 +76,30 @@ int scan_exclusive_u64(const uint64_t* in, uint64_t* out, uint64_t n, Workspace&
     scan_apply_kernel<<<1, SCAN_THREADS, 0, s>>>(in, n, nullptr, out);
     return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
   }
-  uint64_t* part = ws.alloc<uint64_t>(nb);
-  uint64_t* carry = ws.alloc<uint64_t>(nb + 1);
-  if (!ws.ok()) return ST_CUDA;
+  if (level >= sc.levels) return ST_INTERNAL;
+  uint64_t* part = sc.part[level];
+  uint64_t* carry = sc.carry[level];
   {
     ProfScope ps(PROF_SCAN, s);
     scan_reduce_kernel<<<unsigned(nb), SCAN_THREADS, 0, s>>>(in, n, part);
   }
-  const int st = scan_exclusive_u64(part, carry, nb, ws, s);
+  const int st = scan_level(part, carry, nb, sc, level + 1, s);
   if (st) return st;
   ProfScope ps(PROF_SCAN, s);
   scan_apply_kernel<<<unsigned(nb), SCAN_THREADS, 0, s>>>(in, n, carry, out);
   return cudaGetLastError() == cudaSuccess ? ST_OK : ST_CUDA;
+}
+
+int scan_exclusive_u64(const uint64_t* in, uint64_t* out, uint64_t n, const ScanScratch& sc,
+                       cudaStream_t s) {
+  return scan_level(in, out, n, sc, 0, s);
+}
+
+int scan_exclusive_u64(const uint64_t* in, uint64_t* out, uint64_t n, Workspace& ws,
+                       cudaStream_t s) {
+  ScanScratch sc;
+  if (!scan_scratch(n, ws, sc)) return ST_CUDA;
+  return scan_level(in, out, n, sc, 0, s);
 }
 
 }  // namespace kg

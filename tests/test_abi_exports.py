@@ -55,3 +55,26 @@ def test_rgg_grid_level_matches_the_oracle(orc):
     assert lib.kg_rgg_grid(4, 10, 0.1, ctypes.byref(g)) == kg.KG_ERR_ARG
     assert lib.kg_rgg_grid(2, 10, 0.51, ctypes.byref(g)) == kg.KG_ERR_ARG
     assert lib.kg_rgg_grid(2, 1 << 32, 0.1, ctypes.byref(g)) == kg.KG_ERR_RANGE
+
+
+def test_noalloc_scratch_need_is_about_128_bytes_per_tile():
+    """kg_gnm_directed_noalloc_scratch is host logic (the measuring pass of
+    the carve that the no-allocation call runs).  Its need is monotone in the
+    tile count and grows by ~128 B per tile (counts of two tile-tree levels,
+    the scanned offsets, the over-full list and the 96-byte descriptor), so
+    the stated limit of about 2^18 tiles holds: P = 255 chunks at tile depth
+    10 fits the 32 MiB array, P = 256 at the same depth does not."""
+    import paper_1710_07565_gb300 as kg
+    kg.lib()
+    lim = kg.NOALLOC_SCRATCH_BYTES
+    n, m = 1 << 20, 260_000_000
+    fit = kg.kg_gnm_directed_noalloc_scratch(n, m, 255)   # 255 * 2^10 tiles
+    over = kg.kg_gnm_directed_noalloc_scratch(n, m, 256)  # 2^18 tiles
+    assert fit <= lim < over
+    # tile depth d: m ceil(n/P) / n <= 1024 * 2^d; doubling m doubles the tiles
+    a = kg.kg_gnm_directed_noalloc_scratch(n, 1 << 24, 64)   # 64 * 2^8 tiles
+    b = kg.kg_gnm_directed_noalloc_scratch(n, 1 << 25, 64)   # 64 * 2^9 tiles
+    per_tile = (b - a) / (64 * (1 << 8))
+    assert 127 <= per_tile <= 130, per_tile
+    # the instance the old estimate admitted but whose descriptors did not fit
+    assert kg.kg_gnm_directed_noalloc_scratch(1 << 26, 1 << 29, 64) > lim

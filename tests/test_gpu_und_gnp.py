@@ -89,6 +89,47 @@ def test_config2_undirected_gnp(kg, orc):
     assert abs(m - 8 * n) < 6 * (8 * n) ** 0.5
 
 
+# The emit pass walks a tile a second time when its kept pairs overflow its
+# slots (k > slots), and walks every tile twice when the slots would pass
+# 12 GB (slots = 0, what a large kg_gnp_directed call does).  Both branches
+# are forced through the slot-count hook and compared with the oracle.
+@pytest.mark.parametrize("slots", [0, 1, 3])
+@pytest.mark.parametrize("und,n,p,seed,P,id_bytes,k_leaf", GNP_CASES)
+def test_gnp_regenerate_path_bit_exact(kg, orc, slots, und, n, p, seed, P, id_bytes, k_leaf):
+    out, cnt = kg.gnp(und, n, p, seed, P, id_bytes=id_bytes, k_leaf=k_leaf, slots_per_tile=slots)
+    kg.check_device_error()
+    k = int(cnt.item())
+    gu, gv = edges_np(out[:k], id_bytes)
+    ou, ov = orc.gnp(und, n, p, seed, P, k_leaf)
+    assert_same_edges(gu, gv, ou, ov, f"gnp slots={slots} und={und} n={n} p={p} P={P}")
+
+
+@pytest.mark.parametrize("slots", [0, 700])
+def test_config2_regenerate_path(kg, orc, slots):
+    """The n = 2^20, degree-16 instance with every tile walked twice (0 slots)
+    and with 700 slots per tile, below the ~1024 kept pairs of most tiles."""
+    n = 1 << 20
+    p = 16 / (n - 1)
+    out, cnt = kg.gnp(True, n, p, 1, 32, id_bytes=4, slots_per_tile=slots)
+    kg.check_device_error()
+    k = int(cnt.item())
+    gu, gv = edges_np(out[:k], 4)
+    ou, ov = orc.gnp(True, n, p, 1, 32, cap_hint=1 << 25)
+    assert_same_edges(gu, gv, ou, ov, f"config 2, {slots} slots")
+
+
+def test_gnp_directed_regenerate_large_tiles(kg, orc):
+    """Directed, tiles of 2^20 pairs with ~1000 kept pairs each and a handful
+    of slots: nearly every tile overflows and is regenerated."""
+    n, p, P = 40000, 1e-3, 5
+    out, cnt = kg.gnp(False, n, p, 3, P, id_bytes=8, slots_per_tile=5)
+    kg.check_device_error()
+    k = int(cnt.item())
+    gu, gv = edges_np(out[:k], 8)
+    ou, ov = orc.gnp(False, n, p, 3, P, cap_hint=1 << 22)
+    assert_same_edges(gu, gv, ou, ov, "directed, 5 slots")
+
+
 def test_gnp_zero_and_capacity(kg):
     import torch
     s = kg._stream_ptr(None)

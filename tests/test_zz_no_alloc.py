@@ -1,12 +1,14 @@
 """kg_gnm_directed_noalloc: the directed G(n,m) entry point for callers that
-cannot let the library allocate device memory (its scratch is a fixed array
-inside libkg.so).  It must return exactly the bytes of kg_gnm_directed.
+cannot let the library allocate device memory -- a framework whose caching
+allocator already holds the GPU's memory, or a steady-state loop in which
+allocation (which may synchronise the device and has no latency bound) is
+forbidden.  Its scratch is a fixed array inside libkg.so.  It must return
+exactly the bytes of kg_gnm_directed.
 
 This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test.  It calls the C ABI through
 the ctypes binding; the output and status buffers are the caller's.
 """
-import numpy as np
 import pytest
 
 from gpu_util import need_cuda
@@ -53,13 +55,30 @@ def test_two_calls_in_a_row_match_the_allocating_entry_point(kg):
         assert torch.equal(got, want), (n, m, P)
 
 
+def test_largest_admitted_instance_matches(kg):
+    """255 chunks at tile depth 10 (261,120 tiles) fit the array with a few
+    hundred KB to spare; the call runs and equals kg_gnm_directed."""
+    import torch
+    n, m, P = 1 << 20, 260_000_000, 255
+    assert kg.kg_gnm_directed_noalloc_scratch(n, m, P) <= kg.NOALLOC_SCRATCH_BYTES
+    got = _noalloc(kg, n, m, 5, P, 4)
+    want = _reference(kg, n, m, 5, P, 4)
+    assert torch.equal(got, want)
+
+
 def test_sizes_beyond_the_scratch_are_rejected_before_any_work(kg):
     import torch
-    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    status = torch.full((1,), -7, dtype=torch.int32, device="cuda")
     s = kg._stream_ptr(None)
     L = kg.lib()
-    # 2^23 tiles would need ~256 MiB of scratch: rejected synchronously
-    st = L.kg_gnm_directed_noalloc(1 << 36, 1 << 33, 1, 1 << 16, 8, 0, 1 << 33, status.data_ptr(), s)
-    assert st == kg.KG_ERR_RANGE
+    torch.cuda.synchronize()
+    for n, m, P in [(1 << 20, 260_000_000, 256),   # 2^18 tiles: just over
+                    (1 << 26, 1 << 29, 64),        # 2^19 tiles
+                    (1 << 36, 1 << 33, 1 << 16)]:  # 2^23 tiles
+        assert kg.kg_gnm_directed_noalloc_scratch(n, m, P) > kg.NOALLOC_SCRATCH_BYTES
+        st = L.kg_gnm_directed_noalloc(n, m, 1, P, 8, 0, m, status.data_ptr(), s)
+        assert st == kg.KG_ERR_RANGE, (n, m, P)
+    torch.cuda.synchronize()
+    assert int(status.item()) == -7  # rejected synchronously: the status word is untouched
     st = L.kg_gnm_directed_noalloc(100, 50, 1, 4, 4, 0, 50, 0, s)  # no status word
     assert st == kg.KG_ERR_ARG
