@@ -197,10 +197,10 @@ kg_status kg_gnp_binomial_count(int undirected, uint64_t n, double p, uint64_t s
  * Output: the same bytes as kg_gnm_directed with the same arguments.
  * Scratch: one array of KG_NOALLOC_SCRATCH_BYTES bytes compiled into the
  * library as a file-scope __device__ variable; every GPU that loads the
- * library holds it until the process exits.  An instance needs about 128
+ * library holds it until the process exits.  An instance needs about 144
  * bytes per tile (tiles = chunks * 2^d, d the tile-tree depth: the smallest d
- * with m * ceil(n/chunks) / n <= 1024 * 2^d), plus a few KB: up to about 2^18
- * tiles, i.e. m up to about 2.7 * 10^8 at the default leaf size.  The need is
+ * with m * ceil(n/chunks) / n <= 1024 * 2^d), plus a few KB: up to about
+ * 233,000 tiles, i.e. m up to about 2.3 * 10^8 at the default leaf size.  The need is
  * computed by the same code that carves the array (and reported by
  * kg_gnm_directed_noalloc_scratch); an instance that does not fit is
  * rejected with KG_ERR_RANGE before any work is enqueued, and d_status is

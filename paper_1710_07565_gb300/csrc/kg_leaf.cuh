@@ -18,6 +18,8 @@
 //   7. A[r] -> (u, v) -> 16- or 8-byte stores to consecutive output slots,
 //      with the order-independent digest and the row runs when asked.
 #pragma once
+#include <type_traits>
+
 #include "kg_gnm.cuh"
 
 namespace kg {
@@ -79,10 +81,14 @@ static_assert(NB_MIN % (8 * FAST_THREADS) == 0, "whole 16-byte counter groups pe
 // Per-tile parameters, computed for all tiles at once (tile_desc_kernel, or
 // the batched engine's descriptor kernel) so that the leaf blocks start
 // without a serial section.  flags: 0 = sample this tile, 1 = over k_max
-// (left to the re-split kernel), 2 = nothing to do.
+// (left to the re-split kernel), 2 = nothing to do, 3 = left by the sparse
+// leaf kernel to the general one (on the fallback list).  aux0 / aux1:
+// per-tile constants of the directed offset map (lo mod (n-1) and the row of
+// offset lo), zero for the other geometries.
 template <class Ctx>
 struct TileDesc {
   uint64_t lo, L, base, cid, U, W, seed;
+  uint64_t aux0, aux1;
   uint32_t k, nb, tau, bmul, bsh;
   int d, flags;
   Ctx gx;
@@ -102,6 +108,8 @@ __device__ __forceinline__ void desc_fill(TileDesc<Ctx>& td, uint64_t U, int d, 
   td.lo = node_bound(U, td.W, d, d, tau);
   td.L = node_bound(U, td.W, d, d, u128(tau) + 1) - td.lo;
   td.k = uint32_t(k > 0xffffffffull ? 0xffffffffull : k);
+  td.aux0 = 0;
+  td.aux1 = 0;
   td.flags = 2;
   td.nb = NB_MIN;
   td.bmul = 0;
@@ -131,12 +139,36 @@ __device__ __forceinline__ void desc_fill(TileDesc<Ctx>& td, uint64_t U, int d, 
   }
 }
 
+// The sparse leaf kernel (kg_leaf_sparse.cuh) samples tiles of the directed
+// geometry with at most SP_KMAX draws over SP_NB buckets; it is used where
+// Floyd's replacements are rare, and leaves to the general kernel every tile
+// it cannot take (flags 3, or a repeated draw found while sorting).
+constexpr int SP_THREADS = 256;
+constexpr int SP_KMAX = 1536;
+constexpr int SP_PAIRS = SP_KMAX / (2 * SP_THREADS);  // draw pairs per thread
+constexpr uint32_t SP_NB = 2048;
+constexpr int SP_CPT = int(SP_NB) / SP_THREADS;       // bucket counters per thread
+static_assert(SP_CPT == 8, "two 16-byte counter groups per thread");
+static_assert(SP_KMAX % (2 * SP_THREADS) == 0, "whole draw pairs per thread");
+
+// Which tiles of a run the sparse kernel takes (on = 0: none).  ymax = 2^(31+s)
+// (saturated): the directed map's 32-bit quotient estimate needs the in-tile
+// offsets y = (lo mod (n-1)) + x below it.
+struct SparseRoute {
+  int on;
+  uint64_t ymax;
+};
+
+// Descriptors of tiles [0, ntiles) of chunks c_begin... .  Tiles over k_max go
+// to big[0 ..) (count nbig[0]), tiles routed away from the sparse kernel to
+// big[ntiles-1 ...) downwards (count nbig[1]); no tile is on both lists.
 template <class Geom>
 __global__ void __launch_bounds__(256)
     tile_desc_kernel(Geom g, uint64_t c_begin, int d, uint32_t k_max, uint64_t seed,
                      const uint64_t* __restrict__ tile_cnt, const uint64_t* __restrict__ tile_off,
                      uint64_t ntiles, TileDesc<typename Geom::Ctx>* __restrict__ desc,
-                     unsigned long long* big, unsigned long long* nbig, int* err) {
+                     unsigned long long* big, unsigned long long* nbig, int* err,
+                     SparseRoute route) {
   for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < ntiles;
        t += uint64_t(gridDim.x) * blockDim.x) {
     TileDesc<typename Geom::Ctx> td;
@@ -147,6 +179,19 @@ __global__ void __launch_bounds__(256)
     td.cid = g.chunk_id(c);
     td.seed = seed;
     td.gx = g.ctx(c);
+    if constexpr (std::is_same<Geom, DirGeom>::value) {
+      // offset lo of the chunk = row q, column position lo - q (n-1)
+      const uint64_t q = div_q(g.div, td.lo);
+      td.aux0 = td.lo - q * (g.n - 1);
+      td.aux1 = td.gx.r0 + q;
+      if (route.on && td.flags == 0) {
+        const bool mapok = td.aux0 < route.ymax && td.L - 1 < route.ymax - td.aux0;
+        if (td.k > uint32_t(SP_KMAX) || td.L <= SP_NB || !mapok) {
+          td.flags = 3;
+          big[ntiles - 1 - atomicAdd(nbig + 1, 1ull)] = t;
+        }
+      }
+    }
     if (td.flags == 1) big[atomicAdd(nbig, 1ull)] = t;
     desc[t] = td;
   }
@@ -182,12 +227,16 @@ __device__ __forceinline__ int sort_bucket(uint64_t* A, uint32_t s0, uint32_t s1
 }
 
 // TILE_SEED: every tile carries its own seed (batched instances); otherwise
-// the round keys of the one seed come in as a kernel parameter.
+// the round keys of the one seed come in as a kernel parameter.  With nlist
+// set, the kernel samples only the *nlist tiles list[ntiles-1], list[ntiles-2],
+// ... (the sparse kernel's fallback list; flags 0 or 3), else tiles
+// [0, ntiles) with flags 0.
 template <class Geom, class Sink, bool DIGEST, bool TILE_SEED>
 __global__ void __launch_bounds__(FAST_THREADS, 4)
     leaf_fast_kernel(Geom g, Sink sink, int d, RoundKeys rk,
                      const TileDesc<typename Geom::Ctx>* __restrict__ desc, uint64_t ntiles,
-                     int* err, DigestOut dig) {
+                     int* err, DigestOut dig, const unsigned long long* __restrict__ list = nullptr,
+                     const unsigned long long* __restrict__ nlist = nullptr) {
   __shared__ __align__(16) FastSmem sm;
   __shared__ unsigned bh[65];
   __shared__ unsigned long long red_d[FAST_THREADS / 32];
@@ -209,16 +258,20 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
     for (uint32_t w = tid; w < sizeof(Desc) / 4; w += FAST_THREADS) dst[w] = src[w];
   };
 
+  const uint64_t count = nlist ? uint64_t(*nlist) : ntiles;
+  auto tile_at = [&](uint64_t i) { return nlist ? uint64_t(list[ntiles - 1 - i]) : i; };
   for (uint32_t b = tid; b < NB_MAX / 2 + 1; b += FAST_THREADS) sm.hist[b] = 0;
-  if (blockIdx.x < ntiles) stage(blockIdx.x, 0);
+  if (blockIdx.x < count) stage(tile_at(blockIdx.x), 0);
   __syncthreads();
   int cur = 0;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x, cur ^= 1) {
+  for (uint64_t it = blockIdx.x; it < count; it += gridDim.x, cur ^= 1) {
     const Desc& td = s_td[cur];
-    const uint64_t tn = t + gridDim.x;
-    if (td.flags != 0 || !sink.fits(td.base, td.k)) {  // uniform over the block
-      if (td.flags == 0 && tid == 0) set_error(err, ST_CAPACITY);  // the tile is dropped
-      if (tn < ntiles) stage(tn, cur ^ 1);
+    const uint64_t t = tile_at(it);
+    const uint64_t itn = it + gridDim.x;
+    const bool take = td.flags == 0 || (nlist && td.flags == 3);
+    if (!take || !sink.fits(td.base, td.k)) {  // uniform over the block
+      if (take && tid == 0) set_error(err, ST_CAPACITY);  // the tile is dropped
+      if (itn < count) stage(tile_at(itn), cur ^ 1);
       __syncthreads();
       continue;
     }
@@ -285,7 +338,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
     // every thread is past the previous tile: its descriptor slot takes the
     // next tile's (DIGEST: the barriers below publish it, so the tile ends
     // without one of its own)
-    if (DIGEST && tn < ntiles) stage(tn, cur ^ 1);
+    if (DIGEST && itn < count) stage(tile_at(itn), cur ^ 1);
     // ---- 3. exclusive scan of the packed counts: thread tid owns words
     // [tid*per, tid*per + per), per = nb / (2 FAST_THREADS) in {4, 8, ...}
     {
@@ -593,7 +646,7 @@ __global__ void __launch_bounds__(FAST_THREADS, 4)
     }
     if constexpr (!DIGEST) {
       // the emission read A / D, which the next tile's draws overwrite
-      if (tn < ntiles) stage(tn, cur ^ 1);
+      if (itn < count) stage(tile_at(itn), cur ^ 1);
       __syncthreads();
     }
   }

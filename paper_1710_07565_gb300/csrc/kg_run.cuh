@@ -3,6 +3,7 @@
 #pragma once
 #include "kg_internal.h"
 #include "kg_leaf.cuh"
+#include "kg_leaf_sparse.cuh"
 #include "kg_prof.h"
 
 namespace kg {
@@ -46,7 +47,9 @@ struct ChunkRunScratch {
   unsigned long long* digest = nullptr;  // per chunk, when the caller gives none
   unsigned long long* hist = nullptr;    // per chunk x 65, likewise
   TileRec* rec = nullptr;                // per tile run records
-  unsigned long long *big = nullptr, *nbig = nullptr;  // tiles over k_max
+  // tiles over k_max from the front, tiles the sparse kernel leaves to the
+  // general one from the back; nbig[0], nbig[1]: their counts
+  unsigned long long *big = nullptr, *nbig = nullptr;
   TileDesc<Ctx>* desc = nullptr;         // per tile descriptors
 
   // C chunks with tile depth d; digest / hist: whether the caller gives them;
@@ -65,11 +68,25 @@ struct ChunkRunScratch {
       rec = ws.alloc<TileRec>(T);
     }
     big = ws.alloc<unsigned long long>(T);
-    nbig = ws.alloc<unsigned long long>(1);
+    nbig = ws.alloc<unsigned long long>(2);
     desc = ws.alloc<TileDesc<Ctx>>(T);
     return ws.ok();
   }
 };
+
+// Whether the tiles of a directed run go to the sparse leaf kernel: Floyd's
+// replacements must be rare (tile width W >= 2^26 pairs: a 2048-draw tile
+// repeats a draw with probability below 1/32, a 1024-draw one below 1/128)
+// and n - 1 >= 4 for the map's quotient estimate.
+template <class Geom>
+inline bool use_sparse_leaf(const Geom& g, uint64_t c_begin, int d) {
+  if constexpr (std::is_same<Geom, DirGeom>::value) {
+    if (g.n < 5) return false;
+    return tile_width(g.universe(c_begin), d) >= (uint64_t(1) << 26);
+  } else {
+    return false;
+  }
+}
 
 // Tile descriptors + leaf kernels over the T tiles of a run.
 template <class Geom, class Sink, bool DIGEST>
@@ -79,17 +96,42 @@ inline int launch_leaf(const Geom& g, const Sink& sink, uint64_t c_begin, int d,
                        const ChunkRunScratch<typename Geom::Ctx>& sc, cudaStream_t s) {
   unsigned long long* big = sc.big;
   unsigned long long* nbig = sc.nbig;
-  if (cudaMemsetAsync(nbig, 0, sizeof(unsigned long long), s) != cudaSuccess) return ST_CUDA;
+  if (cudaMemsetAsync(nbig, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) return ST_CUDA;
   using Desc = TileDesc<typename Geom::Ctx>;
   Desc* desc = sc.desc;
+  const bool sparse = use_sparse_leaf(g, c_begin, d);
+  SparseRoute route{0, 0};
+  SparseMap mp{};
+  if constexpr (std::is_same<Geom, DirGeom>::value) {
+    if (sparse) {
+      mp = sparse_map(g.n);
+      route = sparse_route(mp, true);
+    }
+  }
   {
     ProfScope ps(PROF_OTHER, s);
     tile_desc_kernel<Geom><<<grid_for(T, 256, sm_count() * 32), 256, 0, s>>>(
-        g, c_begin, d, k_max, seed, tile_cnt, tile_off, T, desc, big, nbig, err);
+        g, c_begin, d, k_max, seed, tile_cnt, tile_off, T, desc, big, nbig, err, route);
     if (launch_ok()) return ST_CUDA;
   }
   const unsigned grid = unsigned(T < 0x7fffffffull ? T : 0x7fffffffull);
-  {
+  if constexpr (std::is_same<Geom, DirGeom>::value) {
+    if (sparse) {
+      {
+        ProfScope ps(PROF_LEAF, s);
+        leaf_sparse_kernel<Sink, DIGEST><<<grid, SP_THREADS, 0, s>>>(
+            mp, sink, round_keys(seed), desc, T, err, dig, big, nbig + 1);
+        if (launch_ok()) return ST_CUDA;
+      }
+      // the tiles the sparse kernel left (usually none): a fixed grid that
+      // reads the list's length on the device
+      ProfScope ps(PROF_OTHER, s);
+      leaf_fast_kernel<Geom, Sink, DIGEST, false><<<sm_count() * 4, FAST_THREADS, 0, s>>>(
+          g, sink, d, round_keys(seed), desc, T, err, dig, big, nbig + 1);
+      if (launch_ok()) return ST_CUDA;
+    }
+  }
+  if (!sparse) {
     ProfScope ps(PROF_LEAF, s);
     leaf_fast_kernel<Geom, Sink, DIGEST, false><<<grid, FAST_THREADS, 0, s>>>(
         g, sink, d, round_keys(seed), desc, T, err, dig);

@@ -57,24 +57,35 @@ def test_rgg_grid_level_matches_the_oracle(orc):
     assert lib.kg_rgg_grid(2, 1 << 32, 0.1, ctypes.byref(g)) == kg.KG_ERR_RANGE
 
 
-def test_noalloc_scratch_need_is_about_128_bytes_per_tile():
+def _largest_fitting_chunks(kg, n, m, lim, top=512):
+    """Largest chunk count <= top whose no-allocation scratch fits `lim`."""
+    for P in range(top, 0, -1):
+        if kg.kg_gnm_directed_noalloc_scratch(n, m, P) <= lim:
+            return P
+    return 0
+
+
+def test_noalloc_scratch_need_per_tile():
     """kg_gnm_directed_noalloc_scratch is host logic (the measuring pass of
-    the carve that the no-allocation call runs).  Its need is monotone in the
-    tile count and grows by ~128 B per tile (counts of two tile-tree levels,
-    the scanned offsets, the over-full list and the 96-byte descriptor), so
-    the stated limit of about 2^18 tiles holds: P = 255 chunks at tile depth
-    10 fits the 32 MiB array, P = 256 at the same depth does not."""
+    the carve that the no-allocation call runs).  Its need grows by ~144 B
+    per tile (counts of two tile-tree levels, the scanned offsets, the tile
+    lists and the 112-byte descriptor), so the 32 MiB array holds about
+    233,000 tiles, and the boundary between fitting and not fitting moves one
+    chunk at a time at a fixed tile depth."""
     import paper_1710_07565_gb300 as kg
     kg.lib()
     lim = kg.NOALLOC_SCRATCH_BYTES
-    n, m = 1 << 20, 260_000_000
-    fit = kg.kg_gnm_directed_noalloc_scratch(n, m, 255)   # 255 * 2^10 tiles
-    over = kg.kg_gnm_directed_noalloc_scratch(n, m, 256)  # 2^18 tiles
-    assert fit <= lim < over
+    n = 1 << 20
     # tile depth d: m ceil(n/P) / n <= 1024 * 2^d; doubling m doubles the tiles
     a = kg.kg_gnm_directed_noalloc_scratch(n, 1 << 24, 64)   # 64 * 2^8 tiles
     b = kg.kg_gnm_directed_noalloc_scratch(n, 1 << 25, 64)   # 64 * 2^9 tiles
     per_tile = (b - a) / (64 * (1 << 8))
-    assert 127 <= per_tile <= 130, per_tile
+    assert 140 <= per_tile <= 148, per_tile
+    # at m = 2.3e8 the tile depth is 10 for 220 <= P <= 256: the largest
+    # fitting chunk count carries about lim / per_tile / 2^10 chunks
+    m = 230_000_000
+    P = _largest_fitting_chunks(kg, n, m, lim, 256)
+    assert abs(P - lim / per_tile / 1024) < 2, P
+    assert kg.kg_gnm_directed_noalloc_scratch(n, m, P + 1) > lim
     # the instance the old estimate admitted but whose descriptors did not fit
     assert kg.kg_gnm_directed_noalloc_scratch(1 << 26, 1 << 29, 64) > lim

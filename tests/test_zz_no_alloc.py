@@ -55,12 +55,21 @@ def test_two_calls_in_a_row_match_the_allocating_entry_point(kg):
         assert torch.equal(got, want), (n, m, P)
 
 
+def _largest_fitting_chunks(kg, n, m):
+    for P in range(256, 0, -1):
+        if kg.kg_gnm_directed_noalloc_scratch(n, m, P) <= kg.NOALLOC_SCRATCH_BYTES:
+            return P
+    return 0
+
+
 def test_largest_admitted_instance_matches(kg):
-    """255 chunks at tile depth 10 (261,120 tiles) fit the array with a few
-    hundred KB to spare; the call runs and equals kg_gnm_directed."""
+    """The largest chunk count whose scratch fits the array at tile depth 10
+    (227 chunks of 2^10 tiles): the call runs and equals
+    kg_gnm_directed."""
     import torch
-    n, m, P = 1 << 20, 260_000_000, 255
-    assert kg.kg_gnm_directed_noalloc_scratch(n, m, P) <= kg.NOALLOC_SCRATCH_BYTES
+    n, m = 1 << 20, 230_000_000
+    P = _largest_fitting_chunks(kg, n, m)
+    assert P > 128
     got = _noalloc(kg, n, m, 5, P, 4)
     want = _reference(kg, n, m, 5, P, 4)
     assert torch.equal(got, want)
@@ -72,9 +81,10 @@ def test_sizes_beyond_the_scratch_are_rejected_before_any_work(kg):
     s = kg._stream_ptr(None)
     L = kg.lib()
     torch.cuda.synchronize()
-    for n, m, P in [(1 << 20, 260_000_000, 256),   # 2^18 tiles: just over
-                    (1 << 26, 1 << 29, 64),        # 2^19 tiles
-                    (1 << 36, 1 << 33, 1 << 16)]:  # 2^23 tiles
+    just_over = _largest_fitting_chunks(kg, 1 << 20, 230_000_000) + 1
+    for n, m, P in [(1 << 20, 230_000_000, just_over),  # one chunk (2^10 tiles) too many
+                    (1 << 26, 1 << 29, 64),             # 2^19 tiles
+                    (1 << 36, 1 << 33, 1 << 16)]:       # 2^23 tiles
         assert kg.kg_gnm_directed_noalloc_scratch(n, m, P) > kg.NOALLOC_SCRATCH_BYTES
         st = L.kg_gnm_directed_noalloc(n, m, 1, P, 8, 0, m, status.data_ptr(), s)
         assert st == kg.KG_ERR_RANGE, (n, m, P)
