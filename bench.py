@@ -337,6 +337,56 @@ def rgg_workload(kg, dim, n, deg, s):
             "bound": "integer ALU (distance tests of the count and emit passes)"}
 
 
+def e1_sweep(kg, sizes=(22, 24, 26, 28), cpu_seconds=2.0):
+    """The paper's sequential G(n,m) shapes (Sec. 8.3: n = m/16, m = 2^22 ..
+    2^28), directed and undirected, on the GPU (whole instance, uint32 ids,
+    P = 64 directed chunks, CUDA events) beside the oracle on
+    one host core (whole chunks of the same instance for directed, whole row
+    blocks for undirected, until about cpu_seconds; edges per second of the
+    sample).  Undirected instances use max(32, m / 2^20) chunks, so that one
+    row block (which regenerates its column chunks) stays a small sample."""
+    import torch
+    import oracle
+    oracle.build()
+    s = torch.cuda.current_stream().cuda_stream
+    rows = []
+    for lg in sizes:
+        m = 1 << lg
+        n = m // 16
+        for und in (False, True):
+            P = max(32, m >> 20) if und else 64
+            entries = 2 * m if und else m
+            out = torch.empty((entries, 2), dtype=torch.int32, device="cuda")
+            f = kg.kg_gnm_undirected if und else kg.kg_gnm_directed
+            ms = _timed(lambda: f(n, m, 1, P, 4, out.data_ptr(), entries, s), 5, warm=2)
+            kg.check_device_error()
+            del out
+            t0 = time.perf_counter()
+            done, parts = 0, 0
+            if und:
+                while parts < P and (parts == 0 or time.perf_counter() - t0 < cpu_seconds):
+                    u, _ = oracle.gnm_undirected_rows(n, m, 1, P, parts, parts + 1)
+                    done += len(u)  # entries (both directions)
+                    parts += 1
+            else:
+                cnt = oracle.gnm_directed_chunk_counts(n, m, 1, P)
+                t0 = time.perf_counter()
+                while parts < P and (parts == 0 or time.perf_counter() - t0 < cpu_seconds):
+                    u, _ = oracle.gnm_directed_chunk(n, m, 1, P, parts, int(cnt[parts]))
+                    done += len(u)
+                    parts += 1
+            cpu_s = time.perf_counter() - t0
+            gpu_rate = entries / ms * 1e3
+            cpu_rate = done / cpu_s
+            rows.append({"m": f"2^{lg}", "n": n, "undirected": und, "chunks": P,
+                         "unit": "entries/s (both directions)" if und else "edges/s",
+                         "gpu_ms": ms, "gpu_rate": gpu_rate, "cpu_rate": cpu_rate,
+                         "gpu_over_cpu": gpu_rate / cpu_rate,
+                         "cpu_sample": f"{parts} of {P} " + ("row blocks" if und else "chunks")})
+    return {"shape": "n = m/16 (Sec. 8.3 sequential and weak-scaling instances)",
+            "cpu": "oracle, one host core: " + _cpu_name(), "rows": rows}
+
+
 def other_workloads(kg, serve_requests=1000):
     """The other configurations, each measured briefly on the same GPU."""
     import torch
@@ -349,6 +399,7 @@ def other_workloads(kg, serve_requests=1000):
     ms = _timed(lambda: kg.kg_gnm_directed(n, m, 1, P, 4, out.data_ptr(), m, s), 20)
     res["gnm_directed_n2e16_m2e20_P64"] = {"ms": ms, "edges_per_s": m / ms * 1e3}
     del out
+    res["e1_sweep"] = e1_sweep(kg)
     # undirected G(n,p), n = 2^20, p = 16/(n-1), 32 x 32 chunks, both directions
     n = 1 << 20
     p = 16 / (n - 1)
@@ -422,7 +473,7 @@ def other_workloads(kg, serve_requests=1000):
             "instances": len(insts), "entries": total, "batched_ms": ms_b, "per_instance_ms": ms_s,
             "speedup": ms_s / ms_b, "graphs_per_s": len(insts) / ms_b * 1e3,
             "entries_per_s": total / ms_b * 1e3, "identical_output": same,
-            "tuned": {"tree_threads": tuning[0], "leaf_grid_cap": tuning[1]}}
+            "tuned": {"tree_threads": tuning[0], "tiles_per_cta": tuning[1]}}
         del out, dig
     finally:
         kg.kg_batch_destroy(h)
@@ -540,6 +591,27 @@ def profile_case(kg, C):
     print(json.dumps({"profile_chunks": C, "edges": k}))
 
 
+def profile_rgg(kg, dim, lg):
+    """RGG(n = 2^lg, 16 expected neighbours, uint32 ids) in `dim` dimensions,
+    sized with kg_rgg_count and generated twice with kg_rgg (the case of the
+    RGG launch lists and edge-pass captures under profiles/)."""
+    import math
+    import torch
+    n = 1 << lg
+    vol = math.pi if dim == 2 else 4 * math.pi / 3
+    r = (16.0 / (vol * (n - 1))) ** (1 / dim)
+    s = torch.cuda.current_stream().cuda_stream
+    cnt = torch.zeros(1, dtype=torch.int64, device="cuda")
+    kg.kg_rgg_count(dim, n, r, 1, cnt.data_ptr(), s)
+    k = int(cnt.item())
+    out = torch.empty((max(k, 1), 2), dtype=torch.int32, device="cuda")
+    for _ in range(2):
+        kg.kg_rgg(dim, n, r, 1, 4, out.data_ptr(), k, cnt.data_ptr(), None, s)
+    torch.cuda.synchronize()
+    kg.check_device_error()
+    print(json.dumps({"profile_rgg": dim, "n": n, "entries": k}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -553,6 +625,9 @@ def main():
     ap.add_argument("--profile-chunks", type=int, default=0,
                     help="run only chunks [0, C) of the workload three times (a small case "
                          "for ncu captures of the leaf kernel) and exit")
+    ap.add_argument("--profile-rgg", type=int, nargs=2, metavar=("DIM", "LOG2N"), default=None,
+                    help="run only RGG(2^LOG2N, 16 neighbours) in DIM dimensions (count pass, "
+                         "then two kg_rgg calls) and exit")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -569,6 +644,8 @@ def main():
     torch.cuda.set_device(local)
     if args.profile_chunks:
         return profile_case(kg, args.profile_chunks)
+    if args.profile_rgg:
+        return profile_rgg(kg, *args.profile_rgg)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 

@@ -243,8 +243,12 @@ kg_status kg_gnm_directed_noalloc_scratch(uint64_t n, uint64_t m, uint32_t chunk
  * (uint32 ids only: id_bytes must be 4).  Limits per instance: chunks <= 64
  * (directed) or <= 32 (undirected), n <= 2^32, m <= 2^44.
  * kg_batch_tune times the launch shapes that do not change the output
- * (threads of the tree kernel, grid of the leaf kernel) on the caller's
- * buffer and keeps the fastest.
+ * (threads per block of the tree kernel: 64, 128, 256; tiles per CTA of the
+ * leaf kernel: 1, 2, 4, 8, 16) on the caller's buffer and keeps the fastest.
+ * Choices are cached for the process by GPU name and size class (log2 of the
+ * instance and tile counts): a batch of a class already tuned on the same GPU
+ * takes the cached choice without timing.  kg_batch_get_tuning reports the
+ * batch's current choice.
  */
 typedef struct kg_instance {
   uint64_t n, m, seed;
@@ -259,7 +263,7 @@ kg_status kg_batch_offsets(const kg_batch* batch, uint64_t* h_offsets /* count +
 kg_status kg_batch_run(kg_batch* batch, void* d_out, uint64_t cap_entries, void* stream);
 kg_status kg_batch_tune(kg_batch* batch, void* d_out, uint64_t cap_entries, int reps, void* stream);
 kg_status kg_batch_get_tuning(const kg_batch* batch, uint32_t* tree_threads,
-                              uint32_t* leaf_grid_cap);
+                              uint32_t* tiles_per_cta);
 kg_status kg_batch_destroy(kg_batch* batch);
 
 /* Exact size of a G(n,p) output before generating it: *d_count (device)

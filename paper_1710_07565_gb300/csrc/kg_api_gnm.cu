@@ -88,7 +88,16 @@ static uint64_t chunk_tree_nodes(const DirParams& dp) { return uint64_t(2) << dp
 
 static int run_chunk_tree(const DirParams& dp, uint64_t seed, uint64_t* cnt, uint64_t* node_cnt,
                           cudaStream_t s, int* err) {
-  for (int l0 = 0; l0 <= dp.D; l0 += 8) {
+  // the top levels one warp per node, level by level; the rest in bands of
+  // 8 levels, one block per subtree root and one thread per node
+  int l = 0;
+  for (; l <= dp.D && (uint64_t(1) << l) <= WARP_TREE_NODES; ++l) {
+    ProfScope ps(PROF_CHUNK_TREE, s);
+    chunk_tree_level_warp<<<grid_for(uint64_t(1) << l, 4, sm_count() * 64), 128, 0, s>>>(
+        RowBounds::make(dp.n, dp.P), seed, dp.m, l, node_cnt, cnt, err);
+    if (launch_ok()) return ST_CUDA;
+  }
+  for (int l0 = l; l0 <= dp.D; l0 += 8) {
     const int l1 = (l0 + 8 < dp.D + 1) ? l0 + 8 : dp.D + 1;
     ProfScope ps(PROF_CHUNK_TREE, s);
     chunk_tree_band<<<unsigned(1) << l0, 256, 0, s>>>(RowBounds::make(dp.n, dp.P), seed, dp.m, l0,

@@ -6,9 +6,14 @@
 // into one CUDA graph and replayed.  The output is the concatenation, in
 // instance order, of what the per-instance entry points write.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "kg.h"
+#include "kg_batch.h"
 #include "kg_run.cuh"
 #include "kg_und.cuh"
 #include "kg_assemble.cuh"
@@ -19,6 +24,11 @@ struct BInst {
   uint64_t n, m, seed;
   uint32_t P, undirected;
   uint32_t big, pad_;  // big: an undirected instance assembled by the per-instance sequence
+  // binom: G(n,p) by binomial chunk counts (Sec. 4.3): the chunk counts are
+  // Binomial(U_c, p) (their sum, m, is known beforehand from the count pass),
+  // and the chunks are then sampled like G(n,m) chunks
+  uint32_t binom, pad2_;
+  double p;
   int d, D;
   uint64_t C;
   uint64_t chunk_base, tile_base, sample_base, pair_base, vert_base, out_base;
@@ -106,9 +116,10 @@ __device__ __forceinline__ uint32_t find_inst(const BInst* __restrict__ inst, ui
   uint32_t a = 0, b = count;
   while (b - a > 1) {
     const uint32_t mid = (a + b) >> 1;
-    const uint64_t v = which == 0 ? inst[mid].tile_base
+    const uint64_t v = which == 0   ? inst[mid].tile_base
                        : which == 1 ? inst[mid].pair_base
-                                    : inst[mid].vert_base;
+                       : which == 2 ? inst[mid].vert_base
+                                    : inst[mid].out_base;
     if (v <= x)
       a = mid;
     else
@@ -128,9 +139,10 @@ __device__ __forceinline__ uint32_t warp_find_inst(const BInst* __restrict__ ins
   i0 = __shfl_sync(0xffffffffu, i0, 0);
   uint64_t nxt = ~uint64_t(0);
   if (i0 + 1 < count)
-    nxt = which == 0 ? inst[i0 + 1].tile_base
+    nxt = which == 0   ? inst[i0 + 1].tile_base
           : which == 1 ? inst[i0 + 1].pair_base
-                       : inst[i0 + 1].vert_base;
+          : which == 2 ? inst[i0 + 1].vert_base
+                       : inst[i0 + 1].out_base;
   return p < nxt ? i0 : find_inst(inst, count, p, which);
 }
 
@@ -164,7 +176,19 @@ __global__ void __launch_bounds__(256)
   const BInst I = inst[blockIdx.x];
   const int tid = threadIdx.x;
   uint64_t* cc = chunk_cnt + I.chunk_base;
-  if (!I.undirected) {
+  if (I.binom) {
+    // as gnp_chunk_counts: chunk c draws Binomial(U_c, p) from (seed, chunk id)
+    for (uint64_t c = tid; c < I.C; c += blockDim.x) {
+      Stream st(I.seed, b_chunk_id(I, c), TAG_GNP_COUNT);
+      uint64_t x = 0;
+      const int e = binomial(b_universe(I, c), I.p, st, x, BINOM_N_MAX);
+      if (e) {
+        set_error(err, e);
+        x = 0;
+      }
+      cc[c] = x;
+    }
+  } else if (!I.undirected) {
     if (tid == 0) node_cnt[1] = I.m;
     __syncthreads();
     for (int level = 0; level <= I.D; ++level) {
@@ -487,6 +511,34 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// ---------------------------------------------------------------- per-instance digests
+// digest[i] += sum of splitmix64(u ^ rotl(v, 32)) over the entries of
+// instance i (kg_edge_digest of its output); a warp takes 32 consecutive
+// entries and adds them with one atomic when they belong to one instance.
+__global__ void __launch_bounds__(256)
+    batch_digests(const BInst* __restrict__ inst, uint32_t count, uint64_t entries,
+                  const uint32_t* __restrict__ out, unsigned long long* __restrict__ dig) {
+  const unsigned lane = threadIdx.x & 31;
+  for (uint64_t p0 = uint64_t(blockIdx.x) * blockDim.x + (threadIdx.x & ~31u); p0 < entries;
+       p0 += uint64_t(gridDim.x) * blockDim.x) {  // uniform over the warp
+    const uint64_t p = p0 + lane;
+    const uint32_t ii = warp_find_inst(inst, count, p < entries ? p : entries - 1, 3, lane);
+    unsigned long long h = 0;
+    if (p < entries) {
+      const uint2 e = reinterpret_cast<const uint2*>(out)[p];
+      h = edge_hash(e.x, e.y);
+    }
+    const uint32_t i0 = __shfl_sync(0xffffffffu, ii, 0);
+    if (__all_sync(0xffffffffu, ii == i0)) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+      if (lane == 0) atomicAdd(&dig[i0], h);
+    } else if (p < entries) {
+      atomicAdd(&dig[ii], h);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- the plan
 struct BatchPlan {
   int device;
@@ -502,8 +554,7 @@ struct BatchPlan {
   uint32_t* pairs_buf;
   unsigned long long *deg, *rowpos, *cursor, *long_rows, *nlong;
   uint64_t* rowptr;
-  void* arena;
-  size_t arena_bytes;
+  ScanScratch scan_t, scan_v;  // the run's two scans (tiles, vertices)
   // undirected instances of at least BIG_PAIRS pairs: assembled one by one
   // with the per-instance sequence (scratch carved from big_arena each time)
   struct Big {
@@ -514,42 +565,147 @@ struct BatchPlan {
   size_t big_arena_bytes = 0;
   // launch shapes chosen by kg_batch_tune (they do not change the output)
   unsigned tree_threads = 256;
-  unsigned leaf_grid_cap = 0x7fffffffu;
-  std::vector<void*> allocs;
+  unsigned tiles_per_cta = 1;
+  unsigned leaf_grid_cap = 0x7fffffffu;  // leaf blocks: ceil(tiles / tiles_per_cta)
+  void* mem = nullptr;  // the plan's device memory (kg_batch_create), one allocation
 };
 
 constexpr uint64_t BIG_PAIRS = uint64_t(1) << 20;
 
 static uint64_t piece(uint64_t b) { return (b + 255) & ~uint64_t(255); }
-static uint64_t scan_scratch(uint64_t n) {
+static uint64_t scan_bytes(uint64_t n) {
   const uint64_t items = 512 * 8, nb = (n + items - 1) / items;
   if (n == 0 || nb == 1) return 0;
-  return piece(nb * 8) + piece((nb + 1) * 8) + scan_scratch(nb);
+  return piece(nb * 8) + piece((nb + 1) * 8) + scan_bytes(nb);
 }
 
-static int plan_alloc(BatchPlan* bp, void** p, uint64_t bytes) {
-  if (cudaMalloc(p, bytes ? bytes : 8) != cudaSuccess) return ST_CUDA;
-  bp->allocs.push_back(*p);
+// Carves the plan's device arrays out of ws in one fixed order (a measuring
+// workspace gives the bytes, a fixed arena the memory).
+static bool plan_carve(BatchPlan& bp, Workspace& ws) {
+  const uint64_t count = bp.count, chunks = bp.chunks, tiles = bp.tiles;
+  const uint64_t pairs = bp.pairs, verts = bp.verts;
+  bp.inst = ws.alloc<BInst>(count);
+  bp.chunk_cnt = ws.alloc<uint64_t>(chunks);
+  bp.tile_tmp = ws.alloc<uint64_t>(tiles);
+  bp.tile_cnt = ws.alloc<uint64_t>(tiles);
+  bp.tile_off = ws.alloc<uint64_t>(tiles + 1);
+  bp.desc = ws.alloc<TileDesc<BatchCtx>>(tiles);
+  bp.big = ws.alloc<unsigned long long>(tiles);
+  bp.nbig = ws.alloc<unsigned long long>(1);
+  bp.pairs_buf = ws.alloc<uint32_t>(2 * pairs);
+  bp.deg = ws.alloc<unsigned long long>(verts);
+  bp.rowptr = ws.alloc<uint64_t>(verts + 1);
+  bp.rowpos = ws.alloc<unsigned long long>(verts);
+  bp.cursor = ws.alloc<unsigned long long>(verts);
+  bp.long_rows = ws.alloc<unsigned long long>(verts);
+  bp.nlong = ws.alloc<unsigned long long>(1);
+  if (!scan_scratch(tiles, ws, bp.scan_t) || !scan_scratch(verts, ws, bp.scan_v)) return false;
+  // scratch of the per-instance assembly (deg, rowptr, cursor, long rows,
+  // count, scan) of the big undirected instances
+  uint64_t nbig = 0;
+  for (const auto& g : bp.bigs) nbig = std::max(nbig, g.n);
+  bp.big_arena_bytes = 0;
+  bp.big_arena = nullptr;
+  if (nbig) {
+    bp.big_arena_bytes = 3 * piece(nbig * 8) + piece((nbig + 1) * 8) + piece(8) +
+                         scan_bytes(nbig) + 512;
+    bp.big_arena = ws.alloc<unsigned char>(bp.big_arena_bytes);
+  }
+  return ws.ok();
+}
+
+// Host-side layout of a batch: validates the instances, fills their table
+// (bases of chunks, tiles, samples, pairs, vertices and output entries, in
+// instance order) and the plan's sizes.  No device memory is touched.
+int batch_layout(const BatchSpec* specs, uint32_t count, std::vector<BInst>& tab, BatchPlan& bp) {
+  tab.assign(count, BInst{});
+  bp.count = count;
+  bp.out_offsets.assign(count + 1, 0);
+  bp.bigs.clear();
+  uint64_t chunks = 0, tiles = 0, samples = 0, pairs = 0, verts = 0, entries = 0;
+  for (uint32_t i = 0; i < count; ++i) {
+    const BatchSpec& q = specs[i];
+    BInst& I = tab[i];
+    I.n = q.n;
+    I.m = q.m;
+    I.seed = q.seed;
+    I.P = q.chunks;
+    I.undirected = q.undirected ? 1 : 0;
+    I.binom = q.binom ? 1 : 0;
+    I.p = q.p;
+    const uint32_t Pmax = I.undirected ? 32u : 64u;
+    if (q.n == 0 || q.chunks == 0 || q.chunks > q.n || q.chunks > Pmax || q.n > (uint64_t(1) << 32))
+      return ST_ARG;
+    const u128 Ntot = I.undirected ? tri_pairs(q.n) : u128(q.n) * (q.n - 1);
+    if (u128(q.m) > Ntot) return ST_ARG;
+    if (q.m > M_MAX) return ST_RANGE;
+    const u128 rmax = (u128(q.n) + q.chunks - 1) / q.chunks;
+    const u128 Unom = I.undirected ? rmax * rmax : rmax * (q.n - 1);
+    if (I.binom) {
+      // as kg_gnp_binomial: chunk universes within the binomial's exact range,
+      // the tile depth from the expected count p U_nom of the nominal chunk
+      if (!(q.p >= 0.0 && q.p <= 1.0)) return ST_ARG;
+      if (Unom > u128(BINOM_N_MAX)) return ST_RANGE;
+      if (tile_depth_e(q.p * dbl(Unom), Unom, K_LEAF, I.d)) return ST_RANGE;
+    } else if (tile_depth(q.m, Unom, Ntot, K_LEAF, I.d)) {
+      return ST_RANGE;
+    }
+    I.D = 0;
+    while ((uint64_t(1) << I.D) < q.chunks) ++I.D;
+    I.C = I.undirected ? uint64_t(q.chunks) * (q.chunks + 1) / 2 : q.chunks;
+    I.rb = RowBounds::make(q.n, q.chunks);
+    I.div = make_div(q.n > 1 ? q.n - 1 : 1);
+    I.chunk_base = chunks;
+    I.tile_base = tiles;
+    I.sample_base = samples;
+    I.pair_base = pairs;
+    I.vert_base = verts;
+    I.out_base = entries;
+    I.big = (I.undirected && q.m >= BIG_PAIRS) ? 1u : 0u;
+    I.pad_ = 0;
+    I.pad2_ = 0;
+    if (I.big) bp.bigs.push_back({q.n, q.m, pairs, entries});
+    bp.out_offsets[i] = entries;
+    chunks += I.C;
+    tiles += I.C << I.d;
+    samples += q.m;
+    if (I.undirected) {
+      pairs += q.m;
+      verts += q.n;
+      entries += 2 * q.m;
+    } else {
+      entries += q.m;
+    }
+  }
+  bp.out_offsets[count] = entries;
+  bp.chunks = chunks;
+  bp.tiles = tiles;
+  bp.samples = samples;
+  bp.pairs = pairs;
+  bp.verts = verts;
+  bp.entries = entries;
+  bp.has_und = pairs > 0;
   return ST_OK;
 }
 
-static void plan_free(BatchPlan* bp) {
-  for (void* p : bp->allocs) cudaFree(p);
-  bp->allocs.clear();
+size_t batch_plan_bytes(BatchPlan& bp) {
+  Workspace meas = Workspace::measuring();
+  BatchPlan copy = bp;
+  if (!plan_carve(copy, meas)) return ~size_t(0);
+  return meas.used();
 }
 
 static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream_t s) {
   int* err = device_error_word();
   if (!err) return ST_CUDA;
   const uint32_t count = bp->count;
-  Workspace ws(s, bp->arena, bp->arena_bytes);
   {
     ProfScope ps(PROF_CHUNK_TREE, s);
     batch_trees<<<count, bp->tree_threads, 0, s>>>(bp->inst, bp->chunk_cnt, bp->tile_tmp,
                                                    bp->tile_cnt, err);
     if (launch_ok()) return ST_CUDA;
   }
-  int st = scan_exclusive_u64(bp->tile_cnt, bp->tile_off, bp->tiles, ws, s);
+  int st = scan_exclusive_u64(bp->tile_cnt, bp->tile_off, bp->tiles, bp->scan_t, s);
   if (st) return st;
   if (cudaMemsetAsync(bp->nbig, 0, 8, s) != cudaSuccess) return ST_CUDA;
   {
@@ -586,7 +742,7 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
                                                                  bp->pairs_buf, bp->deg);
     if (launch_ok()) return ST_CUDA;
   }
-  st = scan_exclusive_u64(reinterpret_cast<const uint64_t*>(bp->deg), bp->rowptr, V, ws, s);
+  st = scan_exclusive_u64(reinterpret_cast<const uint64_t*>(bp->deg), bp->rowptr, V, bp->scan_v, s);
   if (st) return st;
   {
     ProfScope ps(PROF_ASSEMBLY, s);
@@ -626,6 +782,60 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
   return ST_OK;
 }
 
+struct BatchGroup {
+  BatchPlan plan;
+  std::vector<BInst> tab;
+  unsigned long long* dig = nullptr;
+};
+
+int batch_group_prepare(const BatchSpec* specs, uint32_t count, BatchGroup** out,
+                        size_t* dev_bytes, size_t* table_bytes) {
+  BatchGroup* g = new BatchGroup();
+  int st = batch_layout(specs, count, g->tab, g->plan);
+  if (st) {
+    delete g;
+    return st;
+  }
+  if (cudaGetDevice(&g->plan.device) != cudaSuccess) {
+    delete g;
+    return ST_CUDA;
+  }
+  *dev_bytes = batch_plan_bytes(g->plan) + piece(uint64_t(count ? count : 1) * 8);
+  *table_bytes = sizeof(BInst) * count;
+  *out = g;
+  return ST_OK;
+}
+
+int batch_group_launch(BatchGroup* g, void* dev_mem, size_t dev_bytes, void* h_table,
+                       uint32_t* out, uint64_t cap, cudaStream_t s) {
+  BatchPlan& bp = g->plan;
+  Workspace ws(s, dev_mem, dev_bytes);
+  if (!plan_carve(bp, ws)) return ST_INTERNAL;
+  g->dig = ws.alloc<unsigned long long>(bp.count);
+  if (!ws.ok()) return ST_INTERNAL;
+  if (bp.count == 0) return ST_OK;
+  memcpy(h_table, g->tab.data(), sizeof(BInst) * bp.count);
+  if (cudaMemcpyAsync(bp.inst, h_table, sizeof(BInst) * bp.count, cudaMemcpyHostToDevice, s) !=
+          cudaSuccess ||
+      cudaMemsetAsync(g->dig, 0, sizeof(unsigned long long) * bp.count, s) != cudaSuccess)
+    return ST_CUDA;
+  if (bp.entries == 0) return ST_OK;
+  int st = batch_run_impl(&bp, out, cap, s);
+  if (st) return st;
+  ProfScope ps(PROF_DIGEST, s);
+  batch_digests<<<grid_for(bp.entries, 256, sm_count() * 16), 256, 0, s>>>(bp.inst, bp.count,
+                                                                           bp.entries, out, g->dig);
+  return launch_ok();
+}
+
+uint64_t batch_group_offset(const BatchGroup* g, uint32_t i) { return g->plan.out_offsets[i]; }
+
+const uint64_t* batch_group_digests(const BatchGroup* g) {
+  return reinterpret_cast<const uint64_t*>(g->dig);
+}
+
+void batch_group_free(BatchGroup* g) { delete g; }
+
 }  // namespace kg
 
 using namespace kg;
@@ -640,131 +850,35 @@ kg_status kg_batch_create(const kg_instance* h_inst, uint32_t count, int id_byte
                           kg_batch** out_batch) {
   if (!out_batch || (count && !h_inst) || id_bytes != 4) return KG_ERR_ARG;
   *out_batch = nullptr;
-  std::vector<BInst> tab(count);
-  kg_batch* b = new kg_batch();
-  BatchPlan& bp = b->plan;
-  bp.count = count;
-  bp.out_offsets.assign(count + 1, 0);
-  uint64_t chunks = 0, tiles = 0, samples = 0, pairs = 0, verts = 0, entries = 0;
+  std::vector<BatchSpec> specs(count);
   for (uint32_t i = 0; i < count; ++i) {
     const kg_instance& q = h_inst[i];
-    BInst& I = tab[i];
-    I.n = q.n;
-    I.m = q.m;
-    I.seed = q.seed;
-    I.P = q.chunks;
-    I.undirected = q.undirected ? 1 : 0;
-    const uint32_t Pmax = I.undirected ? 32u : 64u;
-    if (q.n == 0 || q.chunks == 0 || q.chunks > q.n || q.chunks > Pmax || q.n > (uint64_t(1) << 32)) {
-      delete b;
-      return KG_ERR_ARG;
-    }
-    const u128 Ntot = I.undirected ? tri_pairs(q.n) : u128(q.n) * (q.n - 1);
-    if (u128(q.m) > Ntot) {
-      delete b;
-      return KG_ERR_ARG;
-    }
-    if (q.m > M_MAX) {
-      delete b;
-      return KG_ERR_RANGE;
-    }
-    const u128 rmax = (u128(q.n) + q.chunks - 1) / q.chunks;
-    const u128 Unom = I.undirected ? rmax * rmax : rmax * (q.n - 1);
-    if (tile_depth(q.m, Unom, Ntot, K_LEAF, I.d)) {
-      delete b;
-      return KG_ERR_RANGE;
-    }
-    I.D = 0;
-    while ((uint64_t(1) << I.D) < q.chunks) ++I.D;
-    I.C = I.undirected ? uint64_t(q.chunks) * (q.chunks + 1) / 2 : q.chunks;
-    I.rb = RowBounds::make(q.n, q.chunks);
-    I.div = make_div(q.n > 1 ? q.n - 1 : 1);
-    I.chunk_base = chunks;
-    I.tile_base = tiles;
-    I.sample_base = samples;
-    I.pair_base = pairs;
-    I.vert_base = verts;
-    I.out_base = entries;
-    I.big = (I.undirected && q.m >= BIG_PAIRS) ? 1u : 0u;
-    I.pad_ = 0;
-    if (I.big) bp.bigs.push_back({q.n, q.m, pairs, entries});
-    bp.out_offsets[i] = entries;
-    chunks += I.C;
-    tiles += I.C << I.d;
-    samples += q.m;
-    if (I.undirected) {
-      pairs += q.m;
-      verts += q.n;
-      entries += 2 * q.m;
-    } else {
-      entries += q.m;
-    }
+    specs[i] = BatchSpec{q.n, q.m, q.seed, 0.0, q.chunks, q.undirected ? 1 : 0, 0};
   }
-  bp.out_offsets[count] = entries;
-  bp.chunks = chunks;
-  bp.tiles = tiles;
-  bp.samples = samples;
-  bp.pairs = pairs;
-  bp.verts = verts;
-  bp.entries = entries;
-  bp.has_und = pairs > 0;
+  kg_batch* b = new kg_batch();
+  BatchPlan& bp = b->plan;
+  std::vector<BInst> tab;
+  int st = batch_layout(specs.data(), count, tab, bp);
+  if (st) {
+    delete b;
+    return kg_status(st);
+  }
   if (cudaGetDevice(&bp.device) != cudaSuccess) {
     delete b;
     return KG_ERR_CUDA;
   }
-  // the plan's device memory, allocated once
-  void* p;
-  int st = ST_OK;
-  auto A = [&](void** dst, uint64_t bytes) {
-    if (!st) st = plan_alloc(&bp, dst, bytes);
-  };
-  A(&p, sizeof(BInst) * (count ? count : 1));
-  bp.inst = static_cast<BInst*>(p);
-  A(&p, chunks * 8);
-  bp.chunk_cnt = static_cast<uint64_t*>(p);
-  A(&p, tiles * 8);
-  bp.tile_tmp = static_cast<uint64_t*>(p);
-  A(&p, tiles * 8);
-  bp.tile_cnt = static_cast<uint64_t*>(p);
-  A(&p, (tiles + 1) * 8);
-  bp.tile_off = static_cast<uint64_t*>(p);
-  A(&p, tiles * sizeof(TileDesc<BatchCtx>));
-  bp.desc = static_cast<TileDesc<BatchCtx>*>(p);
-  A(&p, tiles * 8);
-  bp.big = static_cast<unsigned long long*>(p);
-  A(&p, 8);
-  bp.nbig = static_cast<unsigned long long*>(p);
-  A(&p, pairs * 8);
-  bp.pairs_buf = static_cast<uint32_t*>(p);
-  A(&p, verts * 8);
-  bp.deg = static_cast<unsigned long long*>(p);
-  A(&p, (verts + 1) * 8);
-  bp.rowptr = static_cast<uint64_t*>(p);
-  A(&p, verts * 8);
-  bp.rowpos = static_cast<unsigned long long*>(p);
-  A(&p, verts * 8);
-  bp.cursor = static_cast<unsigned long long*>(p);
-  A(&p, verts * 8);
-  bp.long_rows = static_cast<unsigned long long*>(p);
-  A(&p, 8);
-  bp.nlong = static_cast<unsigned long long*>(p);
-  bp.arena_bytes = scan_scratch(tiles) + scan_scratch(verts) + 512;  // both scans of one run
-  A(&bp.arena, bp.arena_bytes);
-  // scratch of the per-instance assembly (deg, rowptr, cursor, long rows, count, scan)
-  uint64_t nbig = 0;
-  for (const auto& g : bp.bigs) nbig = std::max(nbig, g.n);
-  if (nbig) {
-    bp.big_arena_bytes = 3 * piece(nbig * 8) + piece((nbig + 1) * 8) + piece(8) +
-                         scan_scratch(nbig) + 512;
-    A(&bp.big_arena, bp.big_arena_bytes);
-  }
-  if (!st && cudaMemcpy(bp.inst, tab.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice) !=
-                 cudaSuccess)
-    st = ST_CUDA;
-  if (st) {
-    plan_free(&bp);
+  // the plan's device memory: one allocation, carved as the measuring pass counted
+  const size_t bytes = batch_plan_bytes(bp);
+  if (cudaMalloc(&bp.mem, bytes ? bytes : 256) != cudaSuccess) {
     delete b;
-    return kg_status(st);
+    return KG_ERR_CUDA;
+  }
+  Workspace ws(nullptr, bp.mem, bytes ? bytes : 256);
+  if (!plan_carve(bp, ws) ||
+      cudaMemcpy(bp.inst, tab.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(bp.mem);
+    delete b;
+    return KG_ERR_CUDA;
   }
   *out_batch = b;
   return KG_OK;
@@ -772,7 +886,7 @@ kg_status kg_batch_create(const kg_instance* h_inst, uint32_t count, int id_byte
 
 kg_status kg_batch_destroy(kg_batch* b) {
   if (!b) return KG_OK;
-  plan_free(&b->plan);
+  if (b->plan.mem) cudaFree(b->plan.mem);
   delete b;
   return KG_OK;
 }
@@ -797,25 +911,67 @@ kg_status kg_batch_run(kg_batch* b, void* d_out, uint64_t cap_entries, void* str
 }
 
 // Autotuning over launch shapes that do not change the output: threads per
-// block of the tree kernel and the grid of the leaf kernel (one block per
-// tile, or a persistent grid striding over the tiles).  Each candidate runs
-// `reps` times on `stream`; the fastest is kept in the plan.
+// block of the per-instance tree kernel, and tiles per CTA of the leaf kernel
+// (the leaf grid is ceil(tiles / tiles_per_cta) blocks striding over the
+// tiles; 1 = one block per tile).  Choices are cached for the process, keyed
+// by the GPU's name and the batch's size class (log2 of its instances and of
+// its tiles): a batch of a class already tuned on this GPU takes the cached
+// choice without timing anything.
+namespace {
+struct TuneKey {
+  std::string gpu;
+  int lg_count, lg_tiles;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(gpu, lg_count, lg_tiles) < std::tie(o.gpu, o.lg_count, o.lg_tiles);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<unsigned, unsigned>> g_tune_cache;  // -> (tree threads, tiles per CTA)
+
+int lg_ceil(uint64_t x) {
+  int l = 0;
+  while ((uint64_t(1) << l) < x && l < 63) ++l;
+  return l;
+}
+}  // namespace
+
+static unsigned grid_cap_for(uint64_t tiles, unsigned per_cta) {
+  const uint64_t g = (tiles + per_cta - 1) / per_cta;
+  return unsigned(g < 1 ? 1 : (g > 0x7fffffffull ? 0x7fffffffull : g));
+}
+
 kg_status kg_batch_tune(kg_batch* b, void* d_out, uint64_t cap_entries, int reps, void* stream) {
   if (!b || reps < 1) return KG_ERR_ARG;
   if (cap_entries < b->plan.entries) return KG_ERR_CAPACITY;
   if (b->plan.count == 0 || b->plan.entries == 0) return KG_OK;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const unsigned trees[] = {128, 256};
-  const unsigned grids[] = {0x7fffffffu, unsigned(sm_count()) * 5 * 8, unsigned(sm_count()) * 5 * 2};
+  cudaDeviceProp prop;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    return KG_ERR_CUDA;
+  const TuneKey key{prop.name, lg_ceil(b->plan.count), lg_ceil(b->plan.tiles)};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      b->plan.tree_threads = it->second.first;
+      b->plan.tiles_per_cta = it->second.second;
+      b->plan.leaf_grid_cap = grid_cap_for(b->plan.tiles, it->second.second);
+      return KG_OK;
+    }
+  }
+  const unsigned trees[] = {64, 128, 256};
+  const unsigned per_cta[] = {1, 2, 4, 8, 16};
   float best = 1e30f;
-  unsigned bt = 256, bg = 0x7fffffffu;
+  unsigned bt = 256, bp = 1;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return KG_ERR_CUDA;
   kg_status st = KG_OK;
   for (unsigned tt : trees)
-    for (unsigned gg : grids) {
+    for (unsigned pc : per_cta) {
       b->plan.tree_threads = tt;
-      b->plan.leaf_grid_cap = gg;
+      b->plan.tiles_per_cta = pc;
+      b->plan.leaf_grid_cap = grid_cap_for(b->plan.tiles, pc);
       float total = 0.f;
       for (int r = 0; r < reps && st == KG_OK; ++r) {
         cudaEventRecord(e0, s);
@@ -829,20 +985,25 @@ kg_status kg_batch_tune(kg_batch* b, void* d_out, uint64_t cap_entries, int reps
       if (st == KG_OK && total < best) {
         best = total;
         bt = tt;
-        bg = gg;
+        bp = pc;
       }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->plan.tree_threads = bt;
-  b->plan.leaf_grid_cap = bg;
+  b->plan.tiles_per_cta = bp;
+  b->plan.leaf_grid_cap = grid_cap_for(b->plan.tiles, bp);
+  if (st == KG_OK) {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = std::make_pair(bt, bp);
+  }
   return st;
 }
 
-kg_status kg_batch_get_tuning(const kg_batch* b, uint32_t* tree_threads, uint32_t* leaf_grid_cap) {
+kg_status kg_batch_get_tuning(const kg_batch* b, uint32_t* tree_threads, uint32_t* tiles_per_cta) {
   if (!b) return KG_ERR_ARG;
   if (tree_threads) *tree_threads = b->plan.tree_threads;
-  if (leaf_grid_cap) *leaf_grid_cap = b->plan.leaf_grid_cap;
+  if (tiles_per_cta) *tiles_per_cta = b->plan.tiles_per_cta;
   return KG_OK;
 }
 

@@ -4,6 +4,7 @@
 // sorts it in shared memory and emits (u, v) pairs with coalesced stores.
 #pragma once
 #include "kg_common.cuh"
+#include "kg_warp_variates.cuh"
 
 namespace kg {
 
@@ -65,8 +66,84 @@ static __global__ void chunk_tree_band(RowBounds rb, uint64_t seed, uint64_t m, 
   }
 }
 
+// Level `level` of the directed chunk tree with one warp per node (the top
+// levels, whose few nodes make the tree's dependent FP64 chain): the same
+// split and variate as chunk_tree_band, drawn by the whole warp.
+static __global__ void __launch_bounds__(128)
+    chunk_tree_level_warp(RowBounds rb, uint64_t seed, uint64_t m, int level,
+                          uint64_t* __restrict__ node_cnt, uint64_t* __restrict__ cnt, int* err) {
+  const uint64_t n = rb.n;
+  const uint64_t nodes = uint64_t(1) << level;
+  const unsigned lane = threadIdx.x & 31;
+  const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t j = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; j < nodes;
+       j += nwarps) {
+    const uint64_t h = nodes + j;
+    uint32_t a, b;
+    if (!chunk_range(rb.P, h, level, a, b)) continue;
+    const uint64_t mc = level == 0 ? m : node_cnt[h];
+    if (b - a == 1) {
+      if (lane == 0) cnt[a] = mc;
+      continue;
+    }
+    const uint32_t s = a + (b - a + 1) / 2;
+    const uint64_t ra = rb(a);
+    const u128 N = u128(rb(b) - ra) * (n - 1);
+    const u128 NL = u128(rb(s) - ra) * (n - 1);
+    uint64_t X = 0;
+    const int e = hypergeometric_warp(N, NL, mc, seed, h, TAG_CHUNK_TREE, X);
+    if (lane == 0) {
+      if (e) {
+        set_error(err, e);
+        X = 0;
+      }
+      node_cnt[2 * h] = X;
+      node_cnt[2 * h + 1] = mc - X;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- tile tree
 constexpr uint64_t SMALL_FAIR_BITS = 4096;  // fair-bit counts up to this size stay on one lane
+// levels of at most this many nodes draw one variate per warp
+// (tile_tree_level_warp, chunk_tree_level_warp), larger ones one per lane
+constexpr uint64_t WARP_TREE_NODES = 2048;
+
+// One level of the tile trees with one warp per node: the node and its split
+// as in tile_tree_level, the variate drawn by the whole warp.
+template <class Geom>
+__global__ void __launch_bounds__(128)
+    tile_tree_level_warp(Geom g, uint64_t c_begin, uint64_t C, int d, int level, uint64_t seed,
+                         const uint64_t* __restrict__ in, uint64_t* __restrict__ out, int* err) {
+  const uint64_t total = C << level;
+  const unsigned lane = threadIdx.x & 31;
+  const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t node = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; node < total;
+       node += nwarps) {
+    const uint64_t c = node >> level;
+    const uint64_t j = node & ((uint64_t(1) << level) - 1);
+    const uint64_t cc = c_begin + c;
+    const uint64_t U = g.universe(cc);
+    const uint64_t W = tile_width(U, d);
+    const uint64_t lo = node_bound(U, W, d, level, j);
+    const uint64_t hi = node_bound(U, W, d, level, u128(j) + 1);
+    const uint64_t mid = node_bound(U, W, d, level + 1, u128(2) * j + 1);
+    const uint64_t k = in[node];
+    const uint64_t sid = (g.chunk_id(cc) << 32) | ((uint64_t(1) << level) + j);
+    uint64_t X = 0;
+    const int st = (k > hi - lo) ? ST_INTERNAL
+                                 : hypergeometric_warp(u128(hi - lo), u128(mid - lo), k, seed,
+                                                       sid, TAG_TILE, X);
+    if (lane == 0) {
+      if (st) {
+        set_error(err, st);
+        X = 0;
+      }
+      out[2 * node] = X;
+      out[2 * node + 1] = k - X;
+    }
+  }
+}
 
 // One level of the tile trees of chunks [c_begin, c_begin + C): node (c, j) at
 // `level` with count in[c 2^level + j] splits its universe at the middle tile

@@ -143,12 +143,16 @@ __device__ __forceinline__ void desc_fill(TileDesc<Ctx>& td, uint64_t U, int d, 
 // geometry with at most SP_KMAX draws over SP_NB buckets; it is used where
 // Floyd's replacements are rare, and leaves to the general kernel every tile
 // it cannot take (flags 3, or a repeated draw found while sorting).
-constexpr int SP_THREADS = 256;
+#ifndef KG_SP_THREADS
+#define KG_SP_THREADS 256
+#endif
+constexpr int SP_THREADS = KG_SP_THREADS;
+constexpr int SP_MIN_BLOCKS = SP_THREADS == 256 ? 5 : 6;  // resident blocks per SM
 constexpr int SP_KMAX = 1536;
 constexpr int SP_PAIRS = SP_KMAX / (2 * SP_THREADS);  // draw pairs per thread
 constexpr uint32_t SP_NB = 2048;
 constexpr int SP_CPT = int(SP_NB) / SP_THREADS;       // bucket counters per thread
-static_assert(SP_CPT == 8, "two 16-byte counter groups per thread");
+static_assert(SP_CPT % 4 == 0, "whole 16-byte counter groups per thread");
 static_assert(SP_KMAX % (2 * SP_THREADS) == 0, "whole draw pairs per thread");
 
 // Which tiles of a run the sparse kernel takes (on = 0: none).  ymax = 2^(31+s)

@@ -57,7 +57,7 @@ struct SparseSmem {
 };
 
 template <class Sink, bool DIGEST>
-__global__ void __launch_bounds__(SP_THREADS, 4)
+__global__ void __launch_bounds__(SP_THREADS, SP_MIN_BLOCKS)
     leaf_sparse_kernel(SparseMap mp, Sink sink, RoundKeys rk,
                        const TileDesc<DirGeom::Ctx>* __restrict__ desc, uint64_t ntiles, int* err,
                        DigestOut dig, unsigned long long* __restrict__ list,
@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(SP_THREADS, 4)
   };
   uint4* const cnt4 = reinterpret_cast<uint4*>(sm.cnt);
 
-  cnt4[2 * tid] = make_uint4(0, 0, 0, 0);
-  cnt4[2 * tid + 1] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+  for (int g4 = 0; g4 < SP_CPT / 4; ++g4) cnt4[(SP_CPT / 4) * tid + g4] = make_uint4(0, 0, 0, 0);
   if (DIGEST)
     for (int b = tid; b < 65; b += SP_THREADS) bh[b] = 0;
   if (blockIdx.x < ntiles) stage(blockIdx.x, 0);
@@ -150,14 +150,21 @@ __global__ void __launch_bounds__(SP_THREADS, 4)
     if (tn < ntiles) stage(tn, cur ^ 1);
 
     // ---- 2. bucket starts; buckets with several draws listed in order.
-    // Thread tid owns counters [8 tid, 8 tid + 8); one scan carries the draw
+    // Thread tid owns counters [SP_CPT tid, SP_CPT (tid + 1)); one scan carries the draw
     // count (low 16 bits) and the number of multi-draw buckets (high 16).
     {
-      uint4 c0 = cnt4[2 * tid], c1 = cnt4[2 * tid + 1];
-      const uint32_t cs[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+      uint32_t cs[SP_CPT];
+#pragma unroll
+      for (int g4 = 0; g4 < SP_CPT / 4; ++g4) {
+        const uint4 cg = cnt4[(SP_CPT / 4) * tid + g4];
+        cs[4 * g4] = cg.x;
+        cs[4 * g4 + 1] = cg.y;
+        cs[4 * g4 + 2] = cg.z;
+        cs[4 * g4 + 3] = cg.w;
+      }
       uint32_t pk = 0;
 #pragma unroll
-      for (int j = 0; j < 8; ++j) pk += cs[j] + (cs[j] > 1 ? 0x10000u : 0u);
+      for (int j = 0; j < SP_CPT; ++j) pk += cs[j] + (cs[j] > 1 ? 0x10000u : 0u);
       uint32_t inc = pk;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -166,23 +173,22 @@ __global__ void __launch_bounds__(SP_THREADS, 4)
       }
       if (lane == 31) wsum[wid] = inc;
       __syncthreads();
-      const uint4 wa = reinterpret_cast<const uint4*>(wsum)[0];
-      const uint4 wb = reinterpret_cast<const uint4*>(wsum)[1];
-      const uint32_t ws[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
       uint32_t before = 0;
 #pragma unroll
-      for (int w = 0; w < 8; ++w) before += (w < wid) ? ws[w] : 0u;
+      for (int w = 0; w < SP_THREADS / 32; ++w) before += (w < wid) ? wsum[w] : 0u;
       uint32_t ex = before + inc - pk;
       uint32_t run = ex & 0xffffu, mpos = ex >> 16;
-      uint32_t st[8];
+      uint32_t st[SP_CPT];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < SP_CPT; ++j) {
         st[j] = run;
         if (cs[j] > 1) sm.multi[mpos++] = run | (cs[j] << 16);
         run += cs[j];
       }
-      cnt4[2 * tid] = make_uint4(st[0], st[1], st[2], st[3]);
-      cnt4[2 * tid + 1] = make_uint4(st[4], st[5], st[6], st[7]);
+#pragma unroll
+      for (int g4 = 0; g4 < SP_CPT / 4; ++g4)
+        cnt4[(SP_CPT / 4) * tid + g4] =
+            make_uint4(st[4 * g4], st[4 * g4 + 1], st[4 * g4 + 2], st[4 * g4 + 3]);
       if (tid == SP_THREADS - 1) s_nmulti = mpos;
     }
     __syncthreads();  // starts and the multi list visible
@@ -200,8 +206,8 @@ __global__ void __launch_bounds__(SP_THREADS, 4)
     }
     __syncthreads();
     // the counters are dead: clear them for the next tile
-    cnt4[2 * tid] = make_uint4(0, 0, 0, 0);
-    cnt4[2 * tid + 1] = make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int g4 = 0; g4 < SP_CPT / 4; ++g4) cnt4[(SP_CPT / 4) * tid + g4] = make_uint4(0, 0, 0, 0);
     int dup = 0;
     const uint32_t nmulti = s_nmulti;
     for (uint32_t e = tid; e < nmulti; e += SP_THREADS) {

@@ -159,10 +159,15 @@ int run_chunks_carved(const Geom& g, uint64_t c_begin, uint64_t C, const uint64_
     uint64_t* out = (level & 1) ? sc.B : sc.A;
     const uint64_t nodes = C << level;
     ProfScope ps(PROF_TILE_TREE, s);
-    // one-warp blocks: the top levels hold a few thousand FP64-bound nodes,
-    // which 256-thread blocks would pile onto a few SMs
-    tile_tree_level<Geom><<<grid_for(nodes, 32, sm_count() * 64), 32, 0, s>>>(g, c_begin, C, d, level,
-                                                                       seed, in, out, err);
+    if (nodes <= WARP_TREE_NODES)
+      // few nodes: one warp per variate, so that the level waits for one
+      // variate's chain instead of the slowest of 32 lanes
+      tile_tree_level_warp<Geom><<<grid_for(nodes, 4, sm_count() * 64), 128, 0, s>>>(
+          g, c_begin, C, d, level, seed, in, out, err);
+    else
+      // one-warp blocks, one node per lane: the levels spread over all SMs
+      tile_tree_level<Geom><<<grid_for(nodes, 32, sm_count() * 64), 32, 0, s>>>(
+          g, c_begin, C, d, level, seed, in, out, err);
     if (launch_ok()) return ST_CUDA;
     in = out;
   }

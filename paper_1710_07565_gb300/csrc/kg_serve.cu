@@ -6,11 +6,15 @@
 // first on the device (kg_gnp_count: the same skip walks without storing
 // them; kg_gnp_binomial_count: the chunk binomials of Sec. 4.3).
 // Admitted requests run on a set of streams, so requests that arrive while
-// others are on the GPU overlap with them; a request's output is reduced on
-// the device to its order-independent digest, copied to host memory, and its
-// budget released -- which admits the next waiting requests.  Everything is
-// host-side scheduling around the library's own entry points; the state of
-// every request stays on the device until its digest is read.
+// others are on the GPU overlap with them.  Small G(n,m) and binomial G(n,p)
+// requests (uint32 ids, at most 2^22 entries, chunk counts the batched engine
+// takes) that are admitted together go to the GPU as one group: one batched
+// launch sequence for all of them (the batched engine over a scratch arena
+// the server owns), with one digest per request; larger requests run alone
+// through their entry points.  A request's output is reduced on the device
+// to its order-independent digest, copied to host memory, and its budget
+// released -- which admits the next waiting requests.  The state of every
+// request stays on the device until its digest is read.
 #include <algorithm>
 #include <chrono>
 #include <deque>
@@ -19,11 +23,15 @@
 #include <vector>
 
 #include "kg.h"
+#include "kg_batch.h"
 #include "kg_internal.h"
 
 namespace {
 
 constexpr uint32_t MAX_INFLIGHT = 4096;
+constexpr uint32_t GROUP_MAX = 1024;                    // requests per group
+constexpr uint64_t GROUP_ENTRIES_MAX = uint64_t(1) << 22;  // entries of a grouped request
+constexpr uint64_t STAGE_BYTES = uint64_t(64) << 20;    // pinned staging of the groups
 
 enum ReqState { SIZING, WAITING, RUNNING };
 
@@ -35,6 +43,58 @@ struct Req {
   uint32_t slot = 0;
   cudaEvent_t ev = nullptr;
   double t_submit = 0, t_admit = 0;
+  int64_t group = -1;  // the group it runs in, or -1 (alone)
+  bool solo = false;   // not batchable (set after a failed group layout)
+};
+
+// First-fit allocator over [0, size) in 256-byte units, coalescing on release.
+struct FreeList {
+  std::map<uint64_t, uint64_t> free_;  // offset -> size
+  uint64_t in_use = 0;
+  void init(uint64_t size) { free_[0] = size & ~uint64_t(255); }
+  bool alloc(uint64_t bytes, uint64_t& off) {
+    bytes = (bytes + 255) & ~uint64_t(255);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        off = it->first;
+        const uint64_t rest = it->second - bytes;
+        free_.erase(it);
+        if (rest) free_[off + bytes] = rest;
+        in_use += bytes;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(uint64_t off, uint64_t bytes) {
+    bytes = (bytes + 255) & ~uint64_t(255);
+    in_use -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+// Requests generated together by the batched engine.
+struct Group {
+  std::vector<uint64_t> ids;
+  uint64_t out_off = 0, out_bytes = 0;  // one output block in the budget
+  uint64_t ar_off = 0, ar_bytes = 0;    // scratch in the arena
+  uint64_t pin_off = 0, pin_bytes = 0;  // pinned staging: instance table, then digests
+  uint64_t tab_bytes = 0;
+  cudaEvent_t ev = nullptr;
+  kg::BatchGroup* plan = nullptr;
+  bool failed = false;  // the launch failed: its requests finish with KG_ERR_CUDA
 };
 
 }  // namespace
@@ -44,6 +104,13 @@ struct kg_server {
   unsigned char* pool = nullptr;
   uint64_t budget = 0, in_use = 0;
   std::map<uint64_t, uint64_t> free_;  // offset -> size, coalesced
+  // the groups' scratch (device) and staging (pinned host)
+  unsigned char* arena = nullptr;
+  uint64_t arena_bytes = 0;
+  unsigned char* stage = nullptr;
+  FreeList arena_free, stage_free;
+  std::unordered_map<int64_t, Group> groups;
+  int64_t next_group = 0;
   std::vector<cudaStream_t> streams;
   uint32_t next_stream = 0;
   uint64_t next_id = 0;
@@ -145,9 +212,115 @@ static void finish(kg_server* S, Req& r, kg_status st, kg_result* out) {
   out->t_done_ms = S->now_ms();
   out->status = st;
   out->pad = 0;
-  if (r.state == RUNNING) S->release(r.off, r.bytes);
+  if (r.state == RUNNING && r.group < 0) S->release(r.off, r.bytes);
   if (r.ev) S->free_events.push_back(r.ev);
   S->free_slots.push_back(r.slot);
+}
+
+// Whether a waiting request may join a group: the batched engine's instance
+// limits (uint32 ids, chunks <= 64 directed / 32 undirected, undirected below
+// 2^20 pairs), G(n,m) or binomial G(n,p), and small (the large ones fill the
+// GPU alone).
+static bool batchable(const Req& r) {
+  const kg_request& q = r.q;
+  if (r.solo || q.id_bytes != 4 || (q.model != 0 && q.model != 2)) return false;
+  if (q.n == 0 || q.n > (uint64_t(1) << 32) || q.chunks == 0 || q.chunks > q.n) return false;
+  if (q.chunks > (q.undirected ? 32u : 64u)) return false;
+  if (r.entries > GROUP_ENTRIES_MAX) return false;
+  // undirected instances carry per-vertex assembly arrays in the group's scratch
+  if (q.undirected && (r.entries / 2 >= (uint64_t(1) << 20) || q.n > (uint64_t(1) << 20)))
+    return false;
+  return true;
+}
+
+static void release_group(kg_server* S, Group& g) {
+  if (g.out_bytes) S->release(g.out_off, g.out_bytes);
+  if (g.ar_bytes) S->arena_free.release(g.ar_off, g.ar_bytes);
+  if (g.pin_bytes) S->stage_free.release(g.pin_off, g.pin_bytes);
+  if (g.ev) S->free_events.push_back(g.ev);
+  if (g.plan) kg::batch_group_free(g.plan);
+  g = Group();
+}
+
+// Lays out the requests `ids` as one group and, if its output, scratch and
+// staging fit, launches it.  Returns 1 when launched, 0 when something did
+// not fit now or a group of several was refused (nothing is kept; the caller
+// tries fewer), -1 when a single request cannot be grouped at all (refused by
+// the layout, or larger than the whole scratch arena or staging area): it is
+// then marked to run alone.
+static int try_group(kg_server* S, const std::vector<uint64_t>& ids) {
+  auto refuse = [&]() {
+    if (ids.size() > 1) return 0;
+    S->reqs[ids[0]].solo = true;
+    return -1;
+  };
+  std::vector<kg::BatchSpec> specs;
+  specs.reserve(ids.size());
+  uint64_t entries = 0;
+  for (uint64_t id : ids) {
+    const Req& r = S->reqs[id];
+    const kg_request& q = r.q;
+    const uint64_t pairs = q.undirected ? r.entries / 2 : r.entries;
+    specs.push_back(kg::BatchSpec{q.n, pairs, q.seed, q.model == 2 ? q.p : 0.0, q.chunks,
+                                  q.undirected ? 1 : 0, q.model == 2 ? 1 : 0});
+    entries += r.entries;
+  }
+  Group g;
+  size_t dev_bytes = 0, tab_bytes = 0;
+  if (kg::batch_group_prepare(specs.data(), uint32_t(specs.size()), &g.plan, &dev_bytes,
+                              &tab_bytes) != kg::ST_OK) {
+    g.plan = nullptr;
+    return refuse();
+  }
+  g.out_bytes = entries ? entries * 8 : 256;
+  g.ar_bytes = dev_bytes;
+  g.tab_bytes = (tab_bytes + 255) & ~uint64_t(255);
+  g.pin_bytes = g.tab_bytes + 8 * ids.size();
+  if (g.ar_bytes > S->arena_bytes || g.pin_bytes > STAGE_BYTES) {
+    kg::batch_group_free(g.plan);
+    return refuse();
+  }
+  // each block is taken only if the previous ones were; on a miss the group
+  // keeps exactly the blocks it holds, so that release_group returns those only
+  const bool got_out = S->alloc(g.out_bytes, g.out_off);
+  const bool got_ar = got_out && S->arena_free.alloc(g.ar_bytes, g.ar_off);
+  const bool got_pin = got_ar && S->stage_free.alloc(g.pin_bytes, g.pin_off);
+  if (!got_pin) {
+    if (!got_out) g.out_bytes = 0;
+    if (!got_ar) g.ar_bytes = 0;
+    g.pin_bytes = 0;
+    release_group(S, g);
+    return 0;
+  }
+  int si = 0;
+  cudaStream_t s = S->pick_stream(si);
+  unsigned char* pin = S->stage + g.pin_off;
+  uint32_t* out = reinterpret_cast<uint32_t*>(S->pool + g.out_off);
+  int st = kg::batch_group_launch(g.plan, S->arena + g.ar_off, g.ar_bytes, pin, out, entries, s);
+  if (st == kg::ST_OK &&
+      cudaMemcpyAsync(pin + g.tab_bytes, kg::batch_group_digests(g.plan), 8 * ids.size(),
+                      cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    st = kg::ST_CUDA;
+  g.ev = S->event();
+  if (st == kg::ST_OK && cudaEventRecord(g.ev, s) != cudaSuccess) st = kg::ST_CUDA;
+  const int64_t gid = S->next_group++;
+  const double now = S->now_ms();
+  for (uint64_t id : ids) {
+    Req& r = S->reqs[id];
+    r.state = RUNNING;
+    r.group = gid;
+    r.t_admit = now;
+    r.stream = si;
+  }
+  g.ids = ids;
+  if (st != kg::ST_OK) {
+    // the launch failed: the group finishes with the error once its stream has
+    // passed what was enqueued
+    g.failed = true;
+    cudaStreamSynchronize(s);
+  }
+  S->groups.emplace(gid, std::move(g));
+  return 1;
 }
 
 extern "C" {
@@ -164,6 +337,18 @@ kg_status kg_server_create(uint64_t budget_bytes, uint32_t nstreams, kg_server**
   }
   S->budget = budget_bytes;
   S->free_[0] = budget_bytes & ~uint64_t(255);
+  // scratch for the groups: an eighth of the budget, between 256 MB and 4 GB
+  uint64_t ab = budget_bytes / 8;
+  if (ab < (uint64_t(256) << 20)) ab = uint64_t(256) << 20;
+  if (ab > (uint64_t(4) << 30)) ab = uint64_t(4) << 30;
+  if (cudaMalloc(reinterpret_cast<void**>(&S->arena), ab) != cudaSuccess ||
+      cudaMallocHost(reinterpret_cast<void**>(&S->stage), STAGE_BYTES) != cudaSuccess) {
+    kg_server_destroy(S);
+    return KG_ERR_CUDA;
+  }
+  S->arena_bytes = ab;
+  S->arena_free.init(ab);
+  S->stage_free.init(STAGE_BYTES);
   if (cudaMalloc(reinterpret_cast<void**>(&S->d_slots), 16 * MAX_INFLIGHT) != cudaSuccess ||
       cudaMallocHost(reinterpret_cast<void**>(&S->h_slots), 16 * MAX_INFLIGHT) != cudaSuccess) {
     kg_server_destroy(S);
@@ -190,8 +375,14 @@ kg_status kg_server_destroy(kg_server* S) {
   }
   for (auto& kv : S->reqs)
     if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+  for (auto& kv : S->groups) {
+    if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+    if (kv.second.plan) kg::batch_group_free(kv.second.plan);
+  }
   for (cudaEvent_t e : S->free_events) cudaEventDestroy(e);
   if (S->pool) cudaFree(S->pool);
+  if (S->arena) cudaFree(S->arena);
+  if (S->stage) cudaFreeHost(S->stage);
   if (S->d_slots) cudaFree(S->d_slots);
   if (S->h_slots) cudaFreeHost(S->h_slots);
   delete S;
@@ -264,6 +455,27 @@ kg_status kg_server_poll(kg_server* S, kg_result* out, uint32_t max_out, uint32_
       S->reqs.erase(r.id);
       continue;
     }
+    if (batchable(r)) {
+      // the run of batchable requests at the front of the queue goes as one
+      // group, halved until its output and scratch fit
+      std::vector<uint64_t> cand;
+      for (auto it = S->waiting.begin(); it != S->waiting.end() && cand.size() < GROUP_MAX; ++it) {
+        Req& c = S->reqs[*it];
+        c.bytes = req_bytes(c.q, c.entries);
+        if (!batchable(c) || c.bytes > S->budget) break;
+        cand.push_back(*it);
+      }
+      int got = 0;
+      while (!cand.empty()) {
+        got = try_group(S, cand);
+        if (got != 0) break;
+        cand.resize(cand.size() / 2);
+      }
+      if (got < 0) continue;  // refused by the layout: these requests run alone
+      if (cand.empty()) break;  // nothing fits now: wait for completions
+      for (size_t i = 0; i < cand.size(); ++i) S->waiting.pop_front();
+      continue;
+    }
     if (!S->alloc(r.bytes ? r.bytes : 256, r.off)) break;
     if (!r.bytes) r.bytes = 256;
     S->waiting.pop_front();
@@ -275,10 +487,30 @@ kg_status kg_server_poll(kg_server* S, kg_result* out, uint32_t max_out, uint32_
       S->reqs.erase(r.id);
     }
   }
-  // completions
+  // completions: whole groups, then requests that ran alone
+  std::vector<int64_t> gdone;
+  for (auto& kv : S->groups)
+    if (cudaEventQuery(kv.second.ev) != cudaErrorNotReady) gdone.push_back(kv.first);
+  std::sort(gdone.begin(), gdone.end());
+  for (int64_t gid : gdone) {
+    Group& g = S->groups[gid];
+    if (*n_out + g.ids.size() > max_out) break;
+    const bool ok = !g.failed && cudaEventQuery(g.ev) == cudaSuccess;
+    const uint64_t* dig = reinterpret_cast<const uint64_t*>(S->stage + g.pin_off + g.tab_bytes);
+    for (size_t i = 0; i < g.ids.size(); ++i) {
+      Req& r = S->reqs[g.ids[i]];
+      kg_result* o = out + (*n_out)++;
+      finish(S, r, ok ? KG_OK : KG_ERR_CUDA, o);
+      o->digest = ok ? dig[i] : 0;
+      S->reqs.erase(g.ids[i]);
+    }
+    release_group(S, g);
+    S->groups.erase(gid);
+  }
   std::vector<uint64_t> done;
   for (auto& kv : S->reqs)
-    if (kv.second.state == RUNNING && cudaEventQuery(kv.second.ev) == cudaSuccess)
+    if (kv.second.state == RUNNING && kv.second.group < 0 &&
+        cudaEventQuery(kv.second.ev) == cudaSuccess)
       done.push_back(kv.first);
   std::sort(done.begin(), done.end());
   for (uint64_t id : done) {

@@ -117,3 +117,35 @@ def test_batch_argument_errors(kg):
         assert L.kg_batch_run(h, 0, 5, kg._stream_ptr(None)) == kg.KG_ERR_CAPACITY
     finally:
         kg.kg_batch_destroy(h)
+
+
+def test_tuning_is_cached_by_size_class(kg):
+    """A second batch of the same size class on the same GPU takes the first
+    one's tuned launch shapes without timing (its output unchanged), and every
+    tiles-per-CTA choice writes the same bytes."""
+    import time
+    import torch
+    from paper_1710_07565_gb300 import workloads
+    insts = workloads.batched_instances(4096)[256:384]
+    h1 = kg.kg_batch_create(insts)
+    h2 = kg.kg_batch_create(insts)
+    try:
+        total = kg.kg_batch_entries(h1)
+        seq = _sequential(kg, insts, total)
+        out = torch.zeros((total, 2), dtype=torch.int32, device="cuda")
+        s = kg._stream_ptr(None)
+        kg.kg_batch_tune(h1, out.data_ptr(), total, 1, s)
+        t0 = time.perf_counter()
+        kg.kg_batch_tune(h2, out.data_ptr(), total, 1, s)
+        t_cached = time.perf_counter() - t0
+        assert kg.kg_batch_get_tuning(h1) == kg.kg_batch_get_tuning(h2)
+        assert t_cached < 0.05  # no timing runs
+        out.zero_()
+        kg.kg_batch_run(h2, out.data_ptr(), total, s)
+        kg.check_device_error()
+        assert torch.equal(out, seq)
+        tt, pc = kg.kg_batch_get_tuning(h1)
+        assert tt in (64, 128, 256) and pc in (1, 2, 4, 8, 16)
+    finally:
+        kg.kg_batch_destroy(h1)
+        kg.kg_batch_destroy(h2)
