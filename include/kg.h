@@ -292,7 +292,13 @@ kg_status kg_gnp_size(int undirected, uint64_t n, double p, uint64_t seed, uint3
  * generators' own scratch comes from the device's stream-ordered pool, not
  * from the budget.  A request larger than the whole budget finishes with
  * KG_ERR_CAPACITY.  The digest of a request does not depend on what else is
- * running.  Not thread-safe: one host thread drives a server.
+ * running.  Small requests (model 0 or 2, id_bytes = 4, at most 2^24 entries,
+ * chunks <= 64 directed or <= 32 undirected, undirected n <= 2^20) admitted
+ * in one poll are generated together, as groups of up to 1024, by the batched
+ * engine (kg_batch_run's kernels) in a scratch arena of budget / 8 (clamped
+ * to 256 MB .. 4 GB) allocated beside the budget; a poll may hand out part of
+ * a finished group and the rest at the next poll.  Not thread-safe: one host
+ * thread drives a server.
  */
 typedef struct kg_request {
   int32_t model;      /* 0: G(n,m), 1: G(n,p) by skips (kg_gnp_ex),

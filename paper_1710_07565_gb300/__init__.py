@@ -426,12 +426,14 @@ def kg_server_destroy(h):
     return _call("kg_server_destroy", h)
 
 
-def serve(requests, budget_bytes, streams=8, id_bytes=4, realtime=True, clock=None):
+def serve(requests, budget_bytes, streams=8, id_bytes=4, realtime=True, clock=None, server=None):
     """Drive a server over `requests` (dicts with an 'arrival' time in seconds):
     submit each at its arrival (realtime) or all at once, poll until all are
-    done.  Returns the per-request results (by id order of submission)."""
+    done.  Returns the per-request results (by id order of submission).  With
+    `server` (a kg_server_create handle) that server is used and kept;
+    otherwise one is created for the call and destroyed after it."""
     import time
-    h = kg_server_create(budget_bytes, streams)
+    h = server if server is not None else kg_server_create(budget_bytes, streams)
     results = {}
     try:
         t0 = time.perf_counter()
@@ -447,7 +449,8 @@ def serve(requests, budget_bytes, streams=8, id_bytes=4, realtime=True, clock=No
             if i < len(requests) and realtime:
                 time.sleep(0)
     finally:
-        kg_server_destroy(h)
+        if server is None:
+            kg_server_destroy(h)
     return [results[k] for k in range(len(requests))]
 
 

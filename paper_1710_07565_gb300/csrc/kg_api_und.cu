@@ -4,6 +4,7 @@
 #include <vector>
 
 #include "kg.h"
+#include "kg_batch.h"
 #include "kg_gnp.cuh"
 #include "kg_run.cuh"
 #include "kg_und.cuh"
@@ -316,6 +317,23 @@ static int gnpb_prepare(int undirected, uint64_t n, double p, uint32_t chunks, i
   if (Unom > u128(BINOM_N_MAX)) return ST_RANGE;
   return tile_depth_e(p * dbl(Unom), Unom, K_LEAF, d);
 }
+
+namespace kg {
+int gnpb_check(int undirected, uint64_t n, double p, uint32_t chunks, int id_bytes) {
+  uint64_t C = 0;
+  int d = 0;
+  return gnpb_prepare(undirected, n, p, chunks, id_bytes, C, d);
+}
+
+int gnpb_size_many(const GnpbSizeReq* d_reqs, uint32_t count, uint64_t* d_sizes, cudaStream_t s) {
+  int* err = device_error_word();
+  if (!err) return ST_CUDA;
+  if (count == 0) return ST_OK;
+  ProfScope ps(PROF_CHUNK_TREE, s);
+  gnpb_size_batch<<<grid_for(count, 4, sm_count() * 64), 128, 0, s>>>(d_reqs, count, d_sizes, err);
+  return launch_ok();
+}
+}  // namespace kg
 
 template <class Geom>
 static int gnpb_counts(const Geom& g, uint64_t C, double p, uint64_t seed, uint64_t* cnt,

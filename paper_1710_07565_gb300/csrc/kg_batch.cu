@@ -191,29 +191,33 @@ __global__ void __launch_bounds__(256)
   } else if (!I.undirected) {
     if (tid == 0) node_cnt[1] = I.m;
     __syncthreads();
+    // one warp per node (warp-cooperative variates: P <= 64, so every level
+    // holds at most 32 nodes for the block's warps)
+    const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int level = 0; level <= I.D; ++level) {
-      for (uint64_t j = tid; j < (uint64_t(1) << level); j += blockDim.x) {
+      for (uint64_t j = wid; j < (uint64_t(1) << level); j += nw) {  // uniform over the warp
         const uint64_t h = (uint64_t(1) << level) + j;
         uint32_t a, b;
         if (!chunk_range(I.P, h, level, a, b)) continue;
         const uint64_t mc = node_cnt[h];
         if (b - a == 1) {
-          cc[a] = mc;
+          if (lane == 0) cc[a] = mc;
           continue;
         }
         const uint32_t s = a + (b - a + 1) / 2;
         const uint64_t ra = I.rb(a);
         const u128 N = u128(I.rb(b) - ra) * (I.n - 1);
         const u128 NL = u128(I.rb(s) - ra) * (I.n - 1);
-        Stream st(I.seed, h, TAG_CHUNK_TREE);
         uint64_t X = 0;
-        const int e = hypergeometric(N, NL, mc, st, X);
-        if (e) {
-          set_error(err, e);
-          X = 0;
+        const int e = hypergeometric_warp(N, NL, mc, I.seed, h, TAG_CHUNK_TREE, X);
+        if (lane == 0) {
+          if (e) {
+            set_error(err, e);
+            X = 0;
+          }
+          node_cnt[2 * h] = X;
+          node_cnt[2 * h + 1] = mc - X;
         }
-        node_cnt[2 * h] = X;
-        node_cnt[2 * h + 1] = mc - X;
       }
       __syncthreads();
     }
@@ -308,10 +312,16 @@ __global__ void __launch_bounds__(256)
     return;
   }
   const uint64_t* in = cc;
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int level = 0; level < d; ++level) {
     uint64_t* out = ((d - 1 - level) & 1) ? out_tmp : out_last;
     const uint64_t total = C << level;
-    for (uint64_t node = tid; node < total; node += blockDim.x) {
+    // levels of few nodes: one warp per node (warp-cooperative variates);
+    // wide levels: one thread per node
+    const bool by_warp = total <= 4 * uint64_t(nw);
+    const uint64_t first = by_warp ? wid : uint64_t(tid);
+    const uint64_t step = by_warp ? nw : blockDim.x;
+    for (uint64_t node = first; node < total; node += step) {  // uniform over the warp if by_warp
       const uint64_t c = node >> level;
       const uint64_t j = node & ((uint64_t(1) << level) - 1);
       const uint64_t U = b_universe(I, c);
@@ -320,10 +330,15 @@ __global__ void __launch_bounds__(256)
       const uint64_t hi = node_bound(U, W, d, level, u128(j) + 1);
       const uint64_t mid = node_bound(U, W, d, level + 1, u128(2) * j + 1);
       const uint64_t k = in[node];
+      const uint64_t sid = (b_chunk_id(I, c) << 32) | ((uint64_t(1) << level) + j);
       uint64_t X = 0;
       int e = ST_INTERNAL;
-      if (k <= hi - lo) {
-        Stream st(I.seed, (b_chunk_id(I, c) << 32) | ((uint64_t(1) << level) + j), TAG_TILE);
+      if (by_warp) {
+        if (k <= hi - lo)
+          e = hypergeometric_warp(u128(hi - lo), u128(mid - lo), k, I.seed, sid, TAG_TILE, X);
+        if (lane != 0) continue;
+      } else if (k <= hi - lo) {
+        Stream st(I.seed, sid, TAG_TILE);
         e = hypergeometric(u128(hi - lo), u128(mid - lo), k, st, X);
       }
       if (e) {
@@ -573,11 +588,6 @@ struct BatchPlan {
 constexpr uint64_t BIG_PAIRS = uint64_t(1) << 20;
 
 static uint64_t piece(uint64_t b) { return (b + 255) & ~uint64_t(255); }
-static uint64_t scan_bytes(uint64_t n) {
-  const uint64_t items = 512 * 8, nb = (n + items - 1) / items;
-  if (n == 0 || nb == 1) return 0;
-  return piece(nb * 8) + piece((nb + 1) * 8) + scan_bytes(nb);
-}
 
 // Carves the plan's device arrays out of ws in one fixed order (a measuring
 // workspace gives the bytes, a fixed arena the memory).
@@ -602,13 +612,15 @@ static bool plan_carve(BatchPlan& bp, Workspace& ws) {
   if (!scan_scratch(tiles, ws, bp.scan_t) || !scan_scratch(verts, ws, bp.scan_v)) return false;
   // scratch of the per-instance assembly (deg, rowptr, cursor, long rows,
   // count, scan) of the big undirected instances
-  uint64_t nbig = 0;
-  for (const auto& g : bp.bigs) nbig = std::max(nbig, g.n);
+  // (the largest need over them, measured on assemble()'s own carve; the
+  // instances are assembled one after the other in stream order)
+  uint64_t need = 0;
+  for (const auto& g : bp.bigs)
+    need = std::max<uint64_t>(need, assemble_scratch_bytes(g.n, 2 * g.m));
   bp.big_arena_bytes = 0;
   bp.big_arena = nullptr;
-  if (nbig) {
-    bp.big_arena_bytes = 3 * piece(nbig * 8) + piece((nbig + 1) * 8) + piece(8) +
-                         scan_bytes(nbig) + 512;
+  if (need) {
+    bp.big_arena_bytes = need;
     bp.big_arena = ws.alloc<unsigned char>(bp.big_arena_bytes);
   }
   return ws.ok();

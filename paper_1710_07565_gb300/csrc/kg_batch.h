@@ -37,4 +37,19 @@ uint64_t batch_group_offset(const BatchGroup* g, uint32_t i);
 const uint64_t* batch_group_digests(const BatchGroup* g);
 void batch_group_free(BatchGroup* g);
 
+// Validation of a G(n,p)-by-binomial-counts instance, as kg_gnp_binomial
+// does it (ST_OK or the status it would return).
+int gnpb_check(int undirected, uint64_t n, double p, uint32_t chunks, int id_bytes);
+
+// Entry counts of `count` G(n,p)-by-binomial-counts instances (device array
+// of GnpbSizeReq in, device sizes out), one kernel for all: each equals what
+// kg_gnp_binomial_count writes for the same instance.
+struct GnpbSizeReq {
+  uint64_t n, seed;
+  double p;
+  uint32_t chunks;
+  int undirected;
+};
+int gnpb_size_many(const GnpbSizeReq* d_reqs, uint32_t count, uint64_t* d_sizes, cudaStream_t s);
+
 }  // namespace kg

@@ -7,6 +7,7 @@
 // offsets to (u, v).  A tile with more kept pairs than slots (beyond ~30
 // standard deviations) is regenerated by the emit pass instead.
 #pragma once
+#include "kg_batch.h"
 #include "kg_common.cuh"
 
 namespace kg {
@@ -127,6 +128,51 @@ __global__ void __launch_bounds__(128)
       x = 0;
     }
     cnt[c] = x;
+  }
+}
+
+// One G(n,p)-by-binomial-counts size pass for many instances at once (the
+// serving loop's sizing): instance i is taken by one warp, whose lanes draw
+// the chunk binomials of gnp_chunk_counts (same streams, same universes:
+// chunk boundaries floor(c n / P)) and add them up; sizes[i] is the entry
+// count kg_gnp_binomial writes (twice the pairs when undirected).
+__global__ void __launch_bounds__(128)
+    gnpb_size_batch(const GnpbSizeReq* __restrict__ reqs, uint32_t count,
+                    uint64_t* __restrict__ sizes, int* err) {
+  const unsigned lane = threadIdx.x & 31;
+  const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t i = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < count;
+       i += nwarps) {
+    const GnpbSizeReq q = reqs[i];
+    const uint64_t P = q.chunks;
+    auto rb = [&](uint64_t c) { return uint64_t((u128(c) * q.n) / P); };
+    const uint64_t C = q.undirected ? P * (P + 1) / 2 : P;
+    unsigned long long tot = 0;
+    for (uint64_t c = lane; c < C; c += 32) {
+      uint64_t U, cid;
+      if (q.undirected) {
+        uint32_t a, b;
+        UndGeom::ij(c, a, b);
+        const uint64_t sa = rb(uint64_t(a) + 1) - rb(a);
+        U = (a == b) ? (sa ? uint64_t(u128(sa) * (sa - 1) / 2) : 0)
+                     : sa * (rb(uint64_t(b) + 1) - rb(b));
+        cid = uint64_t(a) * P + b;
+      } else {
+        U = (rb(c + 1) - rb(c)) * (q.n - 1);
+        cid = c;
+      }
+      Stream st(q.seed, cid, TAG_GNP_COUNT);
+      uint64_t x = 0;
+      const int e = binomial(U, q.p, st, x, BINOM_N_MAX);
+      if (e) {
+        set_error(err, e);
+        x = 0;
+      }
+      tot += x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (lane == 0) sizes[i] = q.undirected ? 2 * tot : tot;
   }
 }
 

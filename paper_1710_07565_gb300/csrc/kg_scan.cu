@@ -25,30 +25,58 @@ __global__ void __launch_bounds__(SCAN_THREADS)
   if (threadIdx.x == 0) part[blockIdx.x] = tot;
 }
 
-// Per block: exclusive scan of its items plus the block's carry-in.
+// Per block: exclusive scan of its items plus the block's carry-in.  Warp w
+// owns the 256 consecutive items base + 256 w + [0, 256), read and written in
+// eight coalesced rows of 32 (lane l holds item 32 k + l of row k); each row
+// is scanned across the lanes and carries its total into the next row.
 __global__ void __launch_bounds__(SCAN_THREADS)
     scan_apply_kernel(const uint64_t* __restrict__ in, uint64_t n, const uint64_t* __restrict__ carry,
                       uint64_t* __restrict__ out) {
-  const uint64_t base = uint64_t(blockIdx.x) * SCAN_ITEMS;
-  // thread t owns the SCAN_PER_THREAD consecutive items base + t*PER + k
+  __shared__ uint64_t warp_base[SCAN_THREADS / 32];
+  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint64_t wbase = uint64_t(blockIdx.x) * SCAN_ITEMS + uint64_t(wid) * (32 * SCAN_PER_THREAD);
   uint64_t v[SCAN_PER_THREAD];
-  uint64_t s = 0;
 #pragma unroll
   for (int k = 0; k < SCAN_PER_THREAD; ++k) {
-    const uint64_t i = base + uint64_t(threadIdx.x) * SCAN_PER_THREAD + k;
+    const uint64_t i = wbase + uint64_t(k) * 32 + lane;
     v[k] = i < n ? in[i] : 0;
-    s += v[k];
   }
-  uint64_t tot;
-  uint64_t incl = block_inclusive_scan<SCAN_THREADS>(s, tot);
-  uint64_t run = incl - s + (carry ? carry[blockIdx.x] : 0);
+  // exclusive prefix of every item within the warp's 256
+  uint64_t run = 0;
 #pragma unroll
   for (int k = 0; k < SCAN_PER_THREAD; ++k) {
-    const uint64_t i = base + uint64_t(threadIdx.x) * SCAN_PER_THREAD + k;
-    if (i < n) out[i] = run;
-    run += v[k];
+    uint64_t x = v[k];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= unsigned(o)) x += y;
+    }
+    const uint64_t excl = run + x - v[k];
+    run += __shfl_sync(0xffffffffu, x, 31);
+    v[k] = excl;
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) out[n] = run;
+  // warp totals to warp bases (one warp scans the sixteen totals)
+  if (lane == 0) warp_base[wid] = run;
+  __syncthreads();
+  if (wid == 0) {
+    const uint64_t t = lane < SCAN_THREADS / 32 ? warp_base[lane] : 0;
+    uint64_t x = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= unsigned(o)) x += y;
+    }
+    if (lane < SCAN_THREADS / 32) warp_base[lane] = x - t + (carry ? carry[blockIdx.x] : 0);
+  }
+  __syncthreads();
+  const uint64_t add = warp_base[wid];
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+    const uint64_t i = wbase + uint64_t(k) * 32 + lane;
+    if (i < n) out[i] = v[k] + add;
+  }
+  // the total after the last item
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == SCAN_THREADS - 1) out[n] = run + add;
 }
 
 bool scan_scratch(uint64_t n, Workspace& ws, ScanScratch& sc) {

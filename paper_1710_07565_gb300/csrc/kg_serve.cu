@@ -30,7 +30,7 @@ namespace {
 
 constexpr uint32_t MAX_INFLIGHT = 4096;
 constexpr uint32_t GROUP_MAX = 1024;                    // requests per group
-constexpr uint64_t GROUP_ENTRIES_MAX = uint64_t(1) << 22;  // entries of a grouped request
+constexpr uint64_t GROUP_ENTRIES_MAX = uint64_t(1) << 24;  // entries of a grouped request
 constexpr uint64_t STAGE_BYTES = uint64_t(64) << 20;    // pinned staging of the groups
 
 enum ReqState { SIZING, WAITING, RUNNING };
@@ -43,8 +43,9 @@ struct Req {
   uint32_t slot = 0;
   cudaEvent_t ev = nullptr;
   double t_submit = 0, t_admit = 0;
-  int64_t group = -1;  // the group it runs in, or -1 (alone)
-  bool solo = false;   // not batchable (set after a failed group layout)
+  int64_t group = -1;   // the group it runs in, or -1 (alone)
+  bool solo = false;    // not batchable (set after a failed group layout)
+  bool failed = false;  // its size pass failed: finishes with KG_ERR_CUDA
 };
 
 // First-fit allocator over [0, size) in 256-byte units, coalescing on release.
@@ -95,6 +96,7 @@ struct Group {
   cudaEvent_t ev = nullptr;
   kg::BatchGroup* plan = nullptr;
   bool failed = false;  // the launch failed: its requests finish with KG_ERR_CUDA
+  size_t reported = 0;  // results already handed out (a poll may take part of a group)
 };
 
 }  // namespace
@@ -111,6 +113,15 @@ struct kg_server {
   FreeList arena_free, stage_free;
   std::unordered_map<int64_t, Group> groups;
   int64_t next_group = 0;
+  // binomial G(n,p) requests waiting for their size pass, and size passes in
+  // flight (one kernel for many requests)
+  std::deque<uint64_t> to_size;
+  struct SizeBatch {
+    std::vector<uint64_t> ids;
+    uint64_t ar_off = 0, ar_bytes = 0, pin_off = 0, pin_bytes = 0, sizes_at = 0;
+    cudaEvent_t ev = nullptr;
+  };
+  std::vector<SizeBatch> sizing;
   std::vector<cudaStream_t> streams;
   uint32_t next_stream = 0;
   uint64_t next_id = 0;
@@ -218,9 +229,9 @@ static void finish(kg_server* S, Req& r, kg_status st, kg_result* out) {
 }
 
 // Whether a waiting request may join a group: the batched engine's instance
-// limits (uint32 ids, chunks <= 64 directed / 32 undirected, undirected below
-// 2^20 pairs), G(n,m) or binomial G(n,p), and small (the large ones fill the
-// GPU alone).
+// limits (uint32 ids, chunks <= 64 directed / 32 undirected), G(n,m) or
+// binomial G(n,p), at most 2^24 entries (the large ones fill the GPU alone),
+// undirected at most 2^20 vertices (the group's per-vertex assembly arrays).
 static bool batchable(const Req& r) {
   const kg_request& q = r.q;
   if (r.solo || q.id_bytes != 4 || (q.model != 0 && q.model != 2)) return false;
@@ -228,8 +239,7 @@ static bool batchable(const Req& r) {
   if (q.chunks > (q.undirected ? 32u : 64u)) return false;
   if (r.entries > GROUP_ENTRIES_MAX) return false;
   // undirected instances carry per-vertex assembly arrays in the group's scratch
-  if (q.undirected && (r.entries / 2 >= (uint64_t(1) << 20) || q.n > (uint64_t(1) << 20)))
-    return false;
+  if (q.undirected && q.n > (uint64_t(1) << 20)) return false;
   return true;
 }
 
@@ -323,6 +333,82 @@ static int try_group(kg_server* S, const std::vector<uint64_t>& ids) {
   return 1;
 }
 
+// Launches the collected requests `grp` (admitted in this order) as groups:
+// the largest prefix whose output and scratch fit (halving), again for the
+// rest; what does not fit now goes back to the front of the queue in order,
+// a request the layout refuses goes back marked to run alone.  Returns false
+// if requests went back for lack of space.
+static bool flush_group(kg_server* S, std::vector<uint64_t>& grp) {
+  size_t at = 0;
+  bool all = true;
+  while (at < grp.size()) {
+    std::vector<uint64_t> cand(grp.begin() + at, grp.end());
+    int got = 0;
+    while (!cand.empty()) {
+      got = try_group(S, cand);
+      if (got != 0) break;
+      cand.resize(cand.size() / 2);
+    }
+    if (got == 1) {
+      at += cand.size();
+      continue;
+    }
+    // nothing fits now, or a single request refused (marked solo): the rest
+    // waits at the front of the queue, in order
+    for (size_t i = grp.size(); i > at; --i) S->waiting.push_front(grp[i - 1]);
+    all = got < 0;
+    break;
+  }
+  grp.clear();
+  return all;
+}
+
+// One size pass for the binomial G(n,p) requests waiting for it (up to
+// SIZE_MAX_BATCH): their parameters staged in pinned memory, one kernel, the
+// sizes copied back, one event.
+constexpr uint32_t SIZE_MAX_BATCH = 4096;
+
+static void launch_sizing(kg_server* S) {
+  while (!S->to_size.empty()) {
+    const uint32_t cnt = uint32_t(std::min<size_t>(S->to_size.size(), SIZE_MAX_BATCH));
+    kg_server::SizeBatch b;
+    const uint64_t par = ((sizeof(kg::GnpbSizeReq) * cnt) + 255) & ~uint64_t(255);
+    b.sizes_at = par;
+    b.ar_bytes = b.pin_bytes = par + 8 * uint64_t(cnt);
+    if (!S->arena_free.alloc(b.ar_bytes, b.ar_off)) return;
+    if (!S->stage_free.alloc(b.pin_bytes, b.pin_off)) {
+      S->arena_free.release(b.ar_off, b.ar_bytes);
+      return;
+    }
+    kg::GnpbSizeReq* hp = reinterpret_cast<kg::GnpbSizeReq*>(S->stage + b.pin_off);
+    for (uint32_t i = 0; i < cnt; ++i) {
+      const uint64_t id = S->to_size.front();
+      S->to_size.pop_front();
+      const kg_request& q = S->reqs[id].q;
+      hp[i] = kg::GnpbSizeReq{q.n, q.seed, q.p, q.chunks, q.undirected ? 1 : 0};
+      b.ids.push_back(id);
+    }
+    int si = 0;
+    cudaStream_t s = S->pick_stream(si);
+    unsigned char* dev = S->arena + b.ar_off;
+    bool ok = cudaMemcpyAsync(dev, hp, sizeof(kg::GnpbSizeReq) * cnt, cudaMemcpyHostToDevice, s) ==
+              cudaSuccess;
+    ok = ok && kg::gnpb_size_many(reinterpret_cast<const kg::GnpbSizeReq*>(dev), cnt,
+                                  reinterpret_cast<uint64_t*>(dev + b.sizes_at), s) == kg::ST_OK;
+    ok = ok && cudaMemcpyAsync(S->stage + b.pin_off + b.sizes_at, dev + b.sizes_at, 8 * cnt,
+                               cudaMemcpyDeviceToHost, s) == cudaSuccess;
+    b.ev = S->event();
+    ok = ok && cudaEventRecord(b.ev, s) == cudaSuccess;
+    if (!ok) {
+      // sizes unknown: these requests finish with an error at the next poll
+      cudaStreamSynchronize(s);
+      uint64_t* hs = reinterpret_cast<uint64_t*>(S->stage + b.pin_off + b.sizes_at);
+      for (uint32_t i = 0; i < cnt; ++i) hs[i] = ~uint64_t(0);
+    }
+    S->sizing.push_back(std::move(b));
+  }
+}
+
 extern "C" {
 
 kg_status kg_server_create(uint64_t budget_bytes, uint32_t nstreams, kg_server** out) {
@@ -375,6 +461,8 @@ kg_status kg_server_destroy(kg_server* S) {
   }
   for (auto& kv : S->reqs)
     if (kv.second.ev) cudaEventDestroy(kv.second.ev);
+  for (auto& b : S->sizing)
+    if (b.ev) cudaEventDestroy(b.ev);
   for (auto& kv : S->groups) {
     if (kv.second.ev) cudaEventDestroy(kv.second.ev);
     if (kv.second.plan) kg::batch_group_free(kv.second.plan);
@@ -403,13 +491,20 @@ kg_status kg_server_submit(kg_server* S, const kg_request* q, uint64_t* id_out) 
     r.entries = q->undirected ? 2 * q->m : q->m;
     r.state = WAITING;
     S->waiting.push_back(r.id);
+  } else if (q->model == 2) {
+    // exact size first: binomial requests are sized together at the next poll
+    const int st = kg::gnpb_check(q->undirected, q->n, q->p, q->chunks, q->id_bytes);
+    if (st != kg::ST_OK) {
+      S->free_slots.push_back(r.slot);
+      return kg_status(st);
+    }
+    r.state = SIZING;
+    S->to_size.push_back(r.id);
   } else {
     // exact size first: the count pass, its result copied to pinned memory
     cudaStream_t s = S->pick_stream(r.stream);
-    kg_status st = q->model == 1 ? kg_gnp_count(q->undirected, q->n, q->p, q->seed, q->chunks,
-                                                1024, S->d_slots + 2 * r.slot, s)
-                                 : kg_gnp_binomial_count(q->undirected, q->n, q->p, q->seed,
-                                                         q->chunks, S->d_slots + 2 * r.slot, s);
+    kg_status st = kg_gnp_count(q->undirected, q->n, q->p, q->seed, q->chunks, 1024,
+                                S->d_slots + 2 * r.slot, s);
     if (st == KG_OK &&
         cudaMemcpyAsync(S->h_slots + 2 * r.slot, S->d_slots + 2 * r.slot, 8, cudaMemcpyDeviceToHost,
                         s) != cudaSuccess)
@@ -432,10 +527,32 @@ kg_status kg_server_submit(kg_server* S, const kg_request* q, uint64_t* id_out) 
 kg_status kg_server_poll(kg_server* S, kg_result* out, uint32_t max_out, uint32_t* n_out) {
   if (!S || !n_out || (max_out && !out)) return KG_ERR_ARG;
   *n_out = 0;
+  launch_sizing(S);
   std::vector<uint64_t> sized;
+  // size passes that finished: their requests join the queue (a request whose
+  // size could not be computed finishes with an error)
+  for (size_t bi = 0; bi < S->sizing.size();) {
+    kg_server::SizeBatch& b = S->sizing[bi];
+    if (cudaEventQuery(b.ev) == cudaErrorNotReady) {
+      ++bi;
+      continue;
+    }
+    const uint64_t* hs = reinterpret_cast<const uint64_t*>(S->stage + b.pin_off + b.sizes_at);
+    for (size_t i = 0; i < b.ids.size(); ++i) {
+      Req& r = S->reqs[b.ids[i]];
+      r.failed = hs[i] == ~uint64_t(0);
+      r.entries = r.failed ? 0 : hs[i];
+      r.state = WAITING;
+      sized.push_back(r.id);
+    }
+    S->arena_free.release(b.ar_off, b.ar_bytes);
+    S->stage_free.release(b.pin_off, b.pin_bytes);
+    S->free_events.push_back(b.ev);
+    S->sizing.erase(S->sizing.begin() + bi);
+  }
   for (auto& kv : S->reqs) {
     Req& r = kv.second;
-    if (r.state == SIZING && cudaEventQuery(r.ev) == cudaSuccess) {
+    if (r.state == SIZING && r.ev && cudaEventQuery(r.ev) == cudaSuccess) {
       r.entries = S->h_slots[2 * r.slot];
       S->free_events.push_back(r.ev);
       r.ev = nullptr;
@@ -446,8 +563,16 @@ kg_status kg_server_poll(kg_server* S, kg_result* out, uint32_t max_out, uint32_
   std::sort(sized.begin(), sized.end());
   for (uint64_t id : sized) S->waiting.push_back(id);
   // admission (arrival order; a request larger than the whole budget is refused)
+  std::vector<uint64_t> grp;
   while (!S->waiting.empty() && *n_out < max_out) {
     Req& r = S->reqs[S->waiting.front()];
+    if (r.failed) {
+      S->waiting.pop_front();
+      r.state = WAITING;
+      finish(S, r, KG_ERR_CUDA, out + (*n_out)++);
+      S->reqs.erase(r.id);
+      continue;
+    }
     r.bytes = req_bytes(r.q, r.entries);
     if (r.bytes > S->budget) {
       S->waiting.pop_front();
@@ -456,24 +581,11 @@ kg_status kg_server_poll(kg_server* S, kg_result* out, uint32_t max_out, uint32_
       continue;
     }
     if (batchable(r)) {
-      // the run of batchable requests at the front of the queue goes as one
-      // group, halved until its output and scratch fit
-      std::vector<uint64_t> cand;
-      for (auto it = S->waiting.begin(); it != S->waiting.end() && cand.size() < GROUP_MAX; ++it) {
-        Req& c = S->reqs[*it];
-        c.bytes = req_bytes(c.q, c.entries);
-        if (!batchable(c) || c.bytes > S->budget) break;
-        cand.push_back(*it);
-      }
-      int got = 0;
-      while (!cand.empty()) {
-        got = try_group(S, cand);
-        if (got != 0) break;
-        cand.resize(cand.size() / 2);
-      }
-      if (got < 0) continue;  // refused by the layout: these requests run alone
-      if (cand.empty()) break;  // nothing fits now: wait for completions
-      for (size_t i = 0; i < cand.size(); ++i) S->waiting.pop_front();
+      // the batchable requests of this pass collect into one group, launched
+      // when it is full or when the pass ends
+      S->waiting.pop_front();
+      grp.push_back(r.id);
+      if (grp.size() == GROUP_MAX && !flush_group(S, grp)) break;
       continue;
     }
     if (!S->alloc(r.bytes ? r.bytes : 256, r.off)) break;
@@ -487,6 +599,7 @@ kg_status kg_server_poll(kg_server* S, kg_result* out, uint32_t max_out, uint32_
       S->reqs.erase(r.id);
     }
   }
+  flush_group(S, grp);
   // completions: whole groups, then requests that ran alone
   std::vector<int64_t> gdone;
   for (auto& kv : S->groups)
@@ -494,16 +607,16 @@ kg_status kg_server_poll(kg_server* S, kg_result* out, uint32_t max_out, uint32_
   std::sort(gdone.begin(), gdone.end());
   for (int64_t gid : gdone) {
     Group& g = S->groups[gid];
-    if (*n_out + g.ids.size() > max_out) break;
     const bool ok = !g.failed && cudaEventQuery(g.ev) == cudaSuccess;
     const uint64_t* dig = reinterpret_cast<const uint64_t*>(S->stage + g.pin_off + g.tab_bytes);
-    for (size_t i = 0; i < g.ids.size(); ++i) {
-      Req& r = S->reqs[g.ids[i]];
+    for (; g.reported < g.ids.size() && *n_out < max_out; ++g.reported) {
+      Req& r = S->reqs[g.ids[g.reported]];
       kg_result* o = out + (*n_out)++;
       finish(S, r, ok ? KG_OK : KG_ERR_CUDA, o);
-      o->digest = ok ? dig[i] : 0;
-      S->reqs.erase(g.ids[i]);
+      o->digest = ok ? dig[g.reported] : 0;
+      S->reqs.erase(g.ids[g.reported]);
     }
+    if (g.reported < g.ids.size()) break;  // the rest at the next poll
     release_group(S, g);
     S->groups.erase(gid);
   }

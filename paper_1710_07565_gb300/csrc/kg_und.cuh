@@ -461,3 +461,376 @@ __global__ void __launch_bounds__(256)
 }
 
 }  // namespace kg
+
+namespace kg {
+
+// ---------------------------------------------------------------- bucketed assembly
+// The window's rows are cut into buckets of 2^bsh consecutive rows, sized so
+// that a bucket holds about ASM_TARGET entries.  (1) Every block histograms
+// its contiguous share of the pairs by bucket in shared memory and adds the
+// counts to the global ones; (2) a scan gives every bucket its final range of
+// the output; (3) every block claims, per bucket, a sub-range for its share
+// (one atomic per bucket and block) and scatters its entries there; (4) one
+// CTA per bucket loads the bucket's entries into shared memory, sorts them
+// by row (counting sort) and each row by column, writes them back in order
+// and fills the rows' offsets.  Buckets larger than shared memory are sorted
+// in place in global memory instead.  The result is the same list as the
+// atomic-per-entry assembly: rows hold unique columns, sorted.
+constexpr int ASM_THREADS = 256;
+constexpr uint32_t ASM_TARGET = 2048;    // expected entries per bucket
+constexpr uint32_t ASM_CAP = 4096;       // entries a bucket may hold in shared memory
+constexpr uint32_t ASM_BR_MAX = 2048;    // rows per bucket
+constexpr uint32_t ASM_NB_MAX = 16384;   // buckets (per-block histogram in shared memory)
+constexpr uint32_t ASM_ROW_LANE = 8;     // rows up to this length are sorted by one thread
+constexpr uint32_t ASM_ROW_WARP = 256;   // ... up to this length by one warp, longer by the block
+
+// contiguous share [i0, i1) of the np pairs for block `blk` of `nblk`
+__device__ __forceinline__ void asm_share(uint64_t np, uint32_t blk, uint32_t nblk, uint64_t& i0,
+                                          uint64_t& i1) {
+  const uint64_t per = (np + nblk - 1) / nblk;
+  i0 = uint64_t(blk) * per;
+  i1 = i0 + per < np ? i0 + per : np;
+  if (i0 > np) i0 = np;
+}
+
+template <class Id>
+__global__ void __launch_bounds__(ASM_THREADS)
+    asm_bucket_count(const Id* __restrict__ pairs, const uint64_t* __restrict__ npairs_dev,
+                     uint64_t npairs_host, uint64_t row_lo, uint64_t nrows, int bsh, uint32_t nb,
+                     unsigned long long* __restrict__ bcnt) {
+  extern __shared__ uint32_t hcnt[];
+  for (uint32_t i = threadIdx.x; i < nb; i += ASM_THREADS) hcnt[i] = 0;
+  __syncthreads();
+  uint64_t i0, i1;
+  asm_share(npairs_dev ? *npairs_dev : npairs_host, blockIdx.x, gridDim.x, i0, i1);
+  for (uint64_t i = i0 + threadIdx.x; i < i1; i += ASM_THREADS) {
+    uint64_t u, v;
+    load_pair(pairs, i, u, v);
+    if (u - row_lo < nrows) atomicAdd(&hcnt[(u - row_lo) >> bsh], 1u);
+    if (v - row_lo < nrows) atomicAdd(&hcnt[(v - row_lo) >> bsh], 1u);
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < nb; i += ASM_THREADS)
+    if (hcnt[i]) atomicAdd(&bcnt[i], (unsigned long long)hcnt[i]);
+}
+
+// bcur[b]: entries of bucket b claimed so far (zero before the launch)
+template <class Id>
+__global__ void __launch_bounds__(ASM_THREADS)
+    asm_bucket_scatter(const Id* __restrict__ pairs, const uint64_t* __restrict__ npairs_dev,
+                       uint64_t npairs_host, uint64_t row_lo, uint64_t nrows, int bsh, uint32_t nb,
+                       const uint64_t* __restrict__ boff, unsigned long long* __restrict__ bcur,
+                       Id* __restrict__ out, uint64_t cap, int* err) {
+  extern __shared__ uint32_t hcur[];  // per bucket: this block's count, then its next slot
+  for (uint32_t i = threadIdx.x; i < nb; i += ASM_THREADS) hcur[i] = 0;
+  __syncthreads();
+  uint64_t i0, i1;
+  asm_share(npairs_dev ? *npairs_dev : npairs_host, blockIdx.x, gridDim.x, i0, i1);
+  for (uint64_t i = i0 + threadIdx.x; i < i1; i += ASM_THREADS) {
+    uint64_t u, v;
+    load_pair(pairs, i, u, v);
+    if (u - row_lo < nrows) atomicAdd(&hcur[(u - row_lo) >> bsh], 1u);
+    if (v - row_lo < nrows) atomicAdd(&hcur[(v - row_lo) >> bsh], 1u);
+  }
+  __syncthreads();
+  // the block's sub-range of every bucket, relative to the bucket's start
+  for (uint32_t i = threadIdx.x; i < nb; i += ASM_THREADS)
+    if (hcur[i]) hcur[i] = uint32_t(atomicAdd(&bcur[i], (unsigned long long)hcur[i]));
+  __syncthreads();
+  for (uint64_t i = i0 + threadIdx.x; i < i1; i += ASM_THREADS) {
+    uint64_t u, v;
+    load_pair(pairs, i, u, v);
+    if (u - row_lo < nrows) {
+      const uint32_t b = uint32_t((u - row_lo) >> bsh);
+      const uint64_t p = boff[b] + atomicAdd(&hcur[b], 1u);
+      if (p < cap)
+        store_pair(out, p, u, v);
+      else
+        set_error(err, ST_CAPACITY);
+    }
+    if (v - row_lo < nrows) {
+      const uint32_t b = uint32_t((v - row_lo) >> bsh);
+      const uint64_t p = boff[b] + atomicAdd(&hcur[b], 1u);
+      if (p < cap)
+        store_pair(out, p, v, u);
+      else
+        set_error(err, ST_CAPACITY);
+    }
+  }
+}
+
+struct AsmSmem {
+  uint64_t key[ASM_CAP];   // (row in bucket) << 48 | column, as loaded
+  uint64_t sorted[ASM_CAP];
+  uint32_t rc[ASM_BR_MAX + 1];  // row counts -> row starts -> row cursors
+  uint32_t nlong;
+  uint32_t longrow[ASM_BR_MAX];  // rows longer than ASM_ROW_SHORT
+};
+
+// Sorts row[0, len), len <= 8, by one thread: the 8-input network of
+// lane_sort_row over registers padded with +infinity.
+__device__ __forceinline__ void asm_lane_sort(uint64_t* row, uint32_t len) {
+  uint64_t x[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) x[i] = uint32_t(i) < len ? row[i] : ~uint64_t(0);
+  auto cx = [&](int i, int j) {
+    const uint64_t a = x[i] < x[j] ? x[i] : x[j], c = x[i] < x[j] ? x[j] : x[i];
+    x[i] = a;
+    x[j] = c;
+  };
+  cx(0, 2); cx(1, 3); cx(4, 6); cx(5, 7);
+  cx(0, 4); cx(1, 5); cx(2, 6); cx(3, 7);
+  cx(0, 1); cx(2, 3); cx(4, 5); cx(6, 7);
+  cx(2, 4); cx(3, 5);
+  cx(1, 4); cx(3, 6);
+  cx(1, 2); cx(3, 4); cx(5, 6);
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    if (uint32_t(i) < len) row[i] = x[i];
+}
+
+template <int E>
+__device__ __forceinline__ void asm_warp_sort_e(uint64_t* row, uint32_t len, unsigned lane) {
+  uint64_t x[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t i = lane * E + e;
+    x[e] = i < len ? row[i] : ~uint64_t(0);
+  }
+  warp_bitonic<E>(x, lane);
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t i = lane * E + e;
+    if (i < len) row[i] = x[e];
+  }
+}
+
+// Sorts row[0, len), len <= 256, by the whole warp (every lane calls it).
+__device__ __forceinline__ void asm_warp_sort(uint64_t* row, uint32_t len, unsigned lane) {
+  if (len <= 32)
+    asm_warp_sort_e<1>(row, len, lane);
+  else if (len <= 64)
+    asm_warp_sort_e<2>(row, len, lane);
+  else if (len <= 128)
+    asm_warp_sort_e<4>(row, len, lane);
+  else
+    asm_warp_sort_e<8>(row, len, lane);
+}
+
+// Block-wide bitonic sort of x[0, n) (n <= ASM_CAP) in shared memory, ascending;
+// positions past n act as +infinity (the first step of each merge compares
+// mirrored positions and only moves the smaller value down).
+__device__ __forceinline__ void asm_block_sort(uint64_t* x, uint32_t n) {
+  uint32_t N = 1;
+  int lgN = 0;
+  while (N < n) {
+    N <<= 1;
+    ++lgN;
+  }
+  for (int lk = 1; lk <= lgN; ++lk) {
+    const uint32_t k = 1u << lk;
+    for (uint32_t i = threadIdx.x; i < N / 2; i += ASM_THREADS) {
+      const uint32_t blk = i >> (lk - 1), off = i & (k / 2 - 1);
+      const uint32_t lo = blk * k + off, hi = blk * k + k - 1 - off;
+      if (hi < n && x[hi] < x[lo]) {
+        const uint64_t t = x[lo];
+        x[lo] = x[hi];
+        x[hi] = t;
+      }
+    }
+    __syncthreads();
+    for (int lj = lk - 2; lj >= 0; --lj) {
+      const uint32_t j = 1u << lj;
+      for (uint32_t i = threadIdx.x; i < N / 2; i += ASM_THREADS) {
+        const uint32_t blk = i >> lj, off = i & (j - 1);
+        const uint32_t lo = blk * 2 * j + off, hi = lo + j;
+        if (hi < n && x[hi] < x[lo]) {
+          const uint64_t t = x[lo];
+          x[lo] = x[hi];
+          x[hi] = t;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// One CTA per bucket (grid-stride): the bucket's entries sorted by (row,
+// column) in shared memory, written back in place; rowptr[r] for its rows.
+// Buckets over ASM_CAP entries go to big (sorted by asm_bucket_sort_global).
+template <class Id>
+__global__ void __launch_bounds__(ASM_THREADS)
+    asm_bucket_sort(Id* __restrict__ out, const uint64_t* __restrict__ boff, uint64_t row_lo,
+                    uint64_t nrows, int bsh, uint32_t nb, uint64_t cap,
+                    uint64_t* __restrict__ rowptr, unsigned long long* __restrict__ big,
+                    unsigned long long* __restrict__ nbig) {
+  extern __shared__ __align__(16) unsigned char asm_raw[];
+  AsmSmem& sm = *reinterpret_cast<AsmSmem*>(asm_raw);
+  for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const uint64_t e0 = boff[b], e1 = boff[b + 1];
+    const uint64_t r0 = uint64_t(b) << bsh;
+    const uint32_t nr = uint32_t(nrows - r0 < (uint64_t(1) << bsh) ? nrows - r0 : (1u << bsh));
+    if (e1 > cap) {  // beyond the output (a capacity error was recorded): empty rows
+      const uint64_t z = e0 < cap ? e0 : cap;
+      for (uint32_t r = threadIdx.x; r < nr; r += ASM_THREADS) rowptr[r0 + r] = z;
+      continue;
+    }
+    const uint64_t c64 = e1 - e0;
+    if (c64 > ASM_CAP) {
+      if (threadIdx.x == 0) big[atomicAdd(nbig, 1ull)] = b;
+      continue;
+    }
+    const uint32_t c = uint32_t(c64);
+    for (uint32_t r = threadIdx.x; r <= nr; r += ASM_THREADS) sm.rc[r] = 0;
+    if (threadIdx.x == 0) sm.nlong = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < c; i += ASM_THREADS) {
+      uint64_t u, v;
+      load_pair(out, e0 + i, u, v);
+      const uint32_t rl = uint32_t(u - row_lo - r0);
+      sm.key[i] = (uint64_t(rl) << 48) | v;
+      atomicAdd(&sm.rc[rl], 1u);
+    }
+    __syncthreads();
+    // row starts: exclusive scan of the row counts (one thread per 8 rows)
+    {
+      const uint32_t per = (nr + ASM_THREADS - 1) / ASM_THREADS;
+      const uint32_t a = threadIdx.x * per;
+      uint32_t sum = 0;
+      for (uint32_t q = 0; q < per && a + q < nr; ++q) sum += sm.rc[a + q];
+      uint32_t tot;
+      uint32_t run = block_inclusive_scan<ASM_THREADS>(sum, tot) - sum;
+      for (uint32_t q = 0; q < per && a + q < nr; ++q) {
+        const uint32_t cnt = sm.rc[a + q];
+        sm.rc[a + q] = run;
+        rowptr[r0 + a + q] = e0 + run;
+        if (cnt > ASM_ROW_WARP) sm.longrow[atomicAdd(&sm.nlong, 1u)] = a + q;
+        run += cnt;
+      }
+    }
+    __syncthreads();
+    // counting-sort placement (the order inside a row does not matter yet)
+    for (uint32_t i = threadIdx.x; i < c; i += ASM_THREADS) {
+      const uint64_t k = sm.key[i];
+      sm.sorted[atomicAdd(&sm.rc[uint32_t(k >> 48)], 1u)] = k;
+    }
+    __syncthreads();
+    // rc[r] is now the end of row r.  Every warp takes groups of 32 rows:
+    // rows of at most ASM_ROW_LANE entries are sorted by their own lane, rows
+    // up to ASM_ROW_WARP by the whole warp one after the other (a bitonic
+    // network over registers and shuffles); longer rows wait for the block
+    {
+      const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+      for (uint32_t g = wid * 32; g < nr; g += ASM_THREADS) {  // uniform over the warp
+        const uint32_t r = g + lane;
+        uint32_t s0 = 0, len = 0;
+        if (r < nr) {
+          s0 = r ? sm.rc[r - 1] : 0;
+          len = sm.rc[r] - s0;
+        }
+        if (len >= 2 && len <= ASM_ROW_LANE) asm_lane_sort(sm.sorted + s0, len);
+        unsigned m = __ballot_sync(0xffffffffu, len > ASM_ROW_LANE && len <= ASM_ROW_WARP);
+        while (m) {
+          const int l = __ffs(m) - 1;
+          m &= m - 1;
+          const uint32_t bl = __shfl_sync(0xffffffffu, s0, l), dl = __shfl_sync(0xffffffffu, len, l);
+          asm_warp_sort(sm.sorted + bl, dl, lane);
+        }
+      }
+    }
+    __syncthreads();
+    // long rows by the whole block, one after the other
+    const uint32_t nl = sm.nlong;
+    for (uint32_t l = 0; l < nl; ++l) {
+      const uint32_t r = sm.longrow[l];
+      const uint32_t s1 = sm.rc[r], s0 = r ? sm.rc[r - 1] : 0;
+      asm_block_sort(sm.sorted + s0, s1 - s0);
+    }
+    for (uint32_t i = threadIdx.x; i < c; i += ASM_THREADS) {
+      const uint64_t k = sm.sorted[i];
+      store_pair(out, e0 + i, row_lo + r0 + (k >> 48), k & ((uint64_t(1) << 48) - 1));
+    }
+    __syncthreads();
+  }
+}
+
+// The buckets over ASM_CAP entries: sorted in place in global memory by
+// (row, column) (bitonic, one CTA per bucket), then each row's offset found
+// by binary search.
+template <class Id>
+__global__ void __launch_bounds__(ASM_THREADS)
+    asm_bucket_sort_global(Id* __restrict__ out, const uint64_t* __restrict__ boff,
+                           uint64_t row_lo, uint64_t nrows, int bsh,
+                           uint64_t* __restrict__ rowptr,
+                           const unsigned long long* __restrict__ big,
+                           const unsigned long long* __restrict__ nbig) {
+  const unsigned long long nb = *nbig;
+  for (unsigned long long q = blockIdx.x; q < nb; q += gridDim.x) {
+    const uint32_t b = uint32_t(big[q]);
+    const uint64_t e0 = boff[b], n = boff[b + 1] - e0;
+    const uint64_t r0 = uint64_t(b) << bsh;
+    const uint64_t nr = nrows - r0 < (uint64_t(1) << bsh) ? nrows - r0 : (uint64_t(1) << bsh);
+    auto get = [&](uint64_t i, uint64_t& u, uint64_t& v) { load_pair(out, e0 + i, u, v); };
+    auto less = [](uint64_t u1, uint64_t v1, uint64_t u2, uint64_t v2) {
+      return u1 < u2 || (u1 == u2 && v1 < v2);
+    };
+    uint64_t N = 1;
+    int lgN = 0;
+    while (N < n) {
+      N <<= 1;
+      ++lgN;
+    }
+    for (int lk = 1; lk <= lgN; ++lk) {
+      const uint64_t k = uint64_t(1) << lk;
+      for (uint64_t i = threadIdx.x; i < N / 2; i += ASM_THREADS) {
+        const uint64_t blk = i >> (lk - 1), off = i & (k / 2 - 1);
+        const uint64_t lo = blk * k + off, hi = blk * k + k - 1 - off;
+        if (hi < n) {
+          uint64_t ul, vl, uh, vh;
+          get(lo, ul, vl);
+          get(hi, uh, vh);
+          if (less(uh, vh, ul, vl)) {
+            store_pair(out, e0 + lo, uh, vh);
+            store_pair(out, e0 + hi, ul, vl);
+          }
+        }
+      }
+      __syncthreads();
+      for (int lj = lk - 2; lj >= 0; --lj) {
+        const uint64_t j = uint64_t(1) << lj;
+        for (uint64_t i = threadIdx.x; i < N / 2; i += ASM_THREADS) {
+          const uint64_t blk = i >> lj, off = i & (j - 1);
+          const uint64_t lo = blk * 2 * j + off, hi = lo + j;
+          if (hi < n) {
+            uint64_t ul, vl, uh, vh;
+            get(lo, ul, vl);
+            get(hi, uh, vh);
+            if (less(uh, vh, ul, vl)) {
+              store_pair(out, e0 + lo, uh, vh);
+              store_pair(out, e0 + hi, ul, vl);
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    // first entry of every row of the bucket
+    for (uint64_t r = threadIdx.x; r < nr; r += ASM_THREADS) {
+      const uint64_t row = row_lo + r0 + r;
+      uint64_t a = 0, e = n;
+      while (a < e) {
+        const uint64_t mid = (a + e) >> 1;
+        uint64_t u, v;
+        get(mid, u, v);
+        if (u < row)
+          a = mid + 1;
+        else
+          e = mid;
+      }
+      rowptr[r0 + r] = e0 + a;
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace kg

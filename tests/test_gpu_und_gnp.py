@@ -282,3 +282,15 @@ def test_undirected_rows_at_scale_sampled_blocks(kg, orc):
         lo, hi = b * n // P, (b + 1) * n // P
         assert int(dig[0]) == orc.edge_checksum(ou, ov)
         assert np.array_equal(hist[0], orc.outdegree_hist(ou, lo, hi))
+
+
+def test_bucketed_assembly_whole_graph(kg, orc):
+    """n = 2^22, m = 2^22 (two entries per row): the whole list goes through
+    the bucketed assembly (4096 buckets of 1024 rows, counting sort by row in
+    shared memory) and equals the oracle's."""
+    n, m, P = 1 << 22, 1 << 22, 64
+    t = kg.gnm_undirected(n, m, 3, P, id_bytes=4)
+    kg.check_device_error()
+    gu, gv = edges_np(t, 4)
+    ou, ov = orc.gnm_undirected(n, m, 3, P)
+    assert_same_edges(gu, gv, ou, ov, "bucketed assembly")
