@@ -571,9 +571,28 @@ def serving_vs_sequential(kg, reqs, budget):
     t_seq = time.perf_counter() - t0
     kg.check_device_error()
     same = all((r["entries"], r["digest"]) == a for r, a in zip(served, alone))
-    return {"requests": len(sub), "served_requests_per_s": len(sub) / t_srv,
-            "sequential_requests_per_s": len(sub) / t_seq, "speedup": t_seq / t_srv,
-            "identical_output": same}
+    res = {"requests": len(sub), "served_requests_per_s": len(sub) / t_srv,
+           "sequential_requests_per_s": len(sub) / t_seq, "speedup": t_seq / t_srv,
+           "identical_output": same}
+    # the requests the server runs alone (not groupable: more than 2^24
+    # entries, or undirected with n > 2^20) one after another: each fills the
+    # GPU by itself, so their sequential time bounds the served time from below
+    def is_large(r, a):
+        return a[0] > (1 << 24) or (r["undirected"] and r["n"] > (1 << 20))
+    large = [r for r, a in zip(sub, alone) if is_large(r, a)]
+    if large and len(large) < len(sub):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in large:
+            _request_alone(kg, r, s)
+        torch.cuda.synchronize()
+        t_large = time.perf_counter() - t0
+        res.update({"large_requests": len(large),
+                    "large_entries_share": sum(a[0] for r, a in zip(sub, alone) if is_large(r, a))
+                    / max(1, sum(a[0] for a in alone)),
+                    "sequential_large_only_s": t_large, "served_s": t_srv, "sequential_s": t_seq,
+                    "speedup_bound_large_serial": t_seq / t_large})
+    return res
 
 
 def profile_case(kg, C):

@@ -32,6 +32,11 @@ struct BInst {
   int d, D;
   uint64_t C;
   uint64_t chunk_base, tile_base, sample_base, pair_base, vert_base, out_base;
+  // pairs of the small undirected instances before this one: the small
+  // instances' pairs come first in the pair buffer (pair_base == spair_base
+  // for them), the big ones' after all of them; vert_base counts the small
+  // instances' vertices only
+  uint64_t spair_base;
   RowBounds rb;
   DivU64 div;  // by n-1 (directed)
 };
@@ -117,7 +122,7 @@ __device__ __forceinline__ uint32_t find_inst(const BInst* __restrict__ inst, ui
   while (b - a > 1) {
     const uint32_t mid = (a + b) >> 1;
     const uint64_t v = which == 0   ? inst[mid].tile_base
-                       : which == 1 ? inst[mid].pair_base
+                       : which == 1 ? inst[mid].spair_base
                        : which == 2 ? inst[mid].vert_base
                                     : inst[mid].out_base;
     if (v <= x)
@@ -140,7 +145,7 @@ __device__ __forceinline__ uint32_t warp_find_inst(const BInst* __restrict__ ins
   uint64_t nxt = ~uint64_t(0);
   if (i0 + 1 < count)
     nxt = which == 0   ? inst[i0 + 1].tile_base
-          : which == 1 ? inst[i0 + 1].pair_base
+          : which == 1 ? inst[i0 + 1].spair_base
           : which == 2 ? inst[i0 + 1].vert_base
                        : inst[i0 + 1].out_base;
   return p < nxt ? i0 : find_inst(inst, count, p, which);
@@ -163,13 +168,15 @@ __device__ __forceinline__ uint64_t b_chunk_id(const BInst& I, uint64_t c) {
 }
 
 // ---------------------------------------------------------------- trees
-// One block per instance: the chunk split tree (directed) or quadrant tree
-// (undirected), then the instance's tile tree level by level.
+// One block per instance: the chunk counts, by the chunk split tree
+// (directed), the quadrant tree (undirected) or the chunk binomials (G(n,p));
+// an instance without tile levels (d = 0) copies them to its tile counts.
+// The tile trees follow level by level over all instances (batch_tile_level).
 constexpr int BT_MAXC = 32 * 33 / 2;  // undirected chunks at P <= 32
 
 __global__ void __launch_bounds__(256)
     batch_trees(const BInst* __restrict__ inst, uint64_t* __restrict__ chunk_cnt,
-                uint64_t* __restrict__ tmp, uint64_t* __restrict__ tile_cnt, int* err) {
+                uint64_t* __restrict__ tile_cnt, int* err) {
   __shared__ uint64_t node_cnt[128];
   __shared__ QNode ql[2][BT_MAXC];
   __shared__ uint32_t qn[2];
@@ -302,54 +309,78 @@ __global__ void __launch_bounds__(256)
     }
   }
   __syncthreads();
-  // tile tree: level l reads `in`, writes the next level; the last level lands in tile_cnt
-  const int d = I.d;
-  const uint64_t C = I.C;
-  uint64_t* out_last = tile_cnt + I.tile_base;
-  uint64_t* out_tmp = tmp + I.tile_base;
-  if (d == 0) {
-    for (uint64_t c = tid; c < C; c += blockDim.x) out_last[c] = cc[c];
-    return;
+  if (I.d == 0)
+    for (uint64_t c = tid; c < I.C; c += blockDim.x) tile_cnt[I.tile_base + c] = cc[c];
+}
+
+// Level bases of the tile trees: row L (L < maxd) of `base` holds, for every
+// instance i, the level-L nodes of the instances before i that have a level L
+// (d > L: C 2^L nodes each), and in column count their total.
+__global__ void __launch_bounds__(1024)
+    batch_level_bases(const BInst* __restrict__ inst, uint32_t count, uint64_t* __restrict__ base) {
+  const int L = int(blockIdx.x);
+  uint64_t* b = base + uint64_t(L) * (count + 1);
+  uint64_t carry = 0;
+  for (uint32_t i0 = 0; i0 < count; i0 += 1024) {
+    const uint32_t i = i0 + threadIdx.x;
+    uint64_t x = 0;
+    if (i < count && inst[i].d > L) x = inst[i].C << L;
+    uint64_t tot;
+    const uint64_t incl = block_inclusive_scan<1024>(x, tot);
+    if (i < count) b[i] = carry + incl - x;
+    carry += tot;
   }
-  const uint64_t* in = cc;
-  const unsigned lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int level = 0; level < d; ++level) {
-    uint64_t* out = ((d - 1 - level) & 1) ? out_tmp : out_last;
-    const uint64_t total = C << level;
-    // levels of few nodes: one warp per node (warp-cooperative variates);
-    // wide levels: one thread per node
-    const bool by_warp = total <= 4 * uint64_t(nw);
-    const uint64_t first = by_warp ? wid : uint64_t(tid);
-    const uint64_t step = by_warp ? nw : blockDim.x;
-    for (uint64_t node = first; node < total; node += step) {  // uniform over the warp if by_warp
-      const uint64_t c = node >> level;
-      const uint64_t j = node & ((uint64_t(1) << level) - 1);
-      const uint64_t U = b_universe(I, c);
-      const uint64_t W = tile_width(U, d);
-      const uint64_t lo = node_bound(U, W, d, level, j);
-      const uint64_t hi = node_bound(U, W, d, level, u128(j) + 1);
-      const uint64_t mid = node_bound(U, W, d, level + 1, u128(2) * j + 1);
-      const uint64_t k = in[node];
-      const uint64_t sid = (b_chunk_id(I, c) << 32) | ((uint64_t(1) << level) + j);
-      uint64_t X = 0;
-      int e = ST_INTERNAL;
-      if (by_warp) {
-        if (k <= hi - lo)
-          e = hypergeometric_warp(u128(hi - lo), u128(mid - lo), k, I.seed, sid, TAG_TILE, X);
-        if (lane != 0) continue;
-      } else if (k <= hi - lo) {
-        Stream st(I.seed, sid, TAG_TILE);
-        e = hypergeometric(u128(hi - lo), u128(mid - lo), k, st, X);
-      }
-      if (e) {
-        set_error(err, e);
-        X = 0;
-      }
-      out[2 * node] = X;
-      out[2 * node + 1] = k - X;
+  if (threadIdx.x == 0) b[count] = carry;
+}
+
+// Level L of every instance's tile tree (Sec. 4.1: a node's count splits
+// between its two halves by a hypergeometric draw from the node's own
+// stream), one thread per node over all instances: node t belongs to the
+// instance i with base[i] <= t < base[i + 1].  Level L reads the chunk counts
+// (L = 0) or level L - 1, and writes level L + 1; levels alternate between tmp
+// and tile_cnt so that the last lands in tile_cnt.
+__global__ void __launch_bounds__(256)
+    batch_tile_level(const BInst* __restrict__ inst, uint32_t count, int L,
+                     const uint64_t* __restrict__ base, const uint64_t* __restrict__ chunk_cnt,
+                     uint64_t* __restrict__ tmp, uint64_t* __restrict__ tile_cnt, int* err) {
+  const uint64_t total = base[count];
+  for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < total;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    uint32_t a = 0, b = count;
+    while (b - a > 1) {
+      const uint32_t mid = (a + b) >> 1;
+      if (base[mid] <= t)
+        a = mid;
+      else
+        b = mid;
     }
-    __syncthreads();
-    in = out;
+    const BInst& I = inst[a];
+    const int d = I.d;
+    const uint64_t node = t - base[a];
+    const uint64_t c = node >> L;
+    const uint64_t j = node & ((uint64_t(1) << L) - 1);
+    const uint64_t* in =
+        L == 0 ? chunk_cnt + I.chunk_base : (((d - L) & 1) ? tmp : tile_cnt) + I.tile_base;
+    uint64_t* out = (((d - 1 - L) & 1) ? tmp : tile_cnt) + I.tile_base;
+    const uint64_t U = b_universe(I, c);
+    const uint64_t W = tile_width(U, d);
+    const uint64_t lo = node_bound(U, W, d, L, j);
+    const uint64_t hi = node_bound(U, W, d, L, u128(j) + 1);
+    const uint64_t mid = node_bound(U, W, d, L + 1, u128(2) * j + 1);
+    const uint64_t k = in[node];
+    const uint64_t sid = (b_chunk_id(I, c) << 32) | ((uint64_t(1) << L) + j);
+    uint64_t X = 0;
+    int e = ST_INTERNAL;
+    if (k <= hi - lo) {
+      Stream st(I.seed, sid, TAG_TILE);
+      e = hypergeometric(u128(hi - lo), u128(mid - lo), k, st, X);
+    }
+    if (e) {
+      set_error(err, e);
+      X = 0;
+    }
+    out[2 * node] = X;
+    out[2 * node + 1] = k - X;
   }
 }
 
@@ -559,11 +590,14 @@ struct BatchPlan {
   int device;
   uint32_t count;
   uint64_t tiles, chunks, pairs, verts, entries, samples;
+  uint64_t spairs;  // pairs of the small undirected instances (the first spairs of the buffer)
+  std::vector<uint64_t> level_nodes;  // tile-tree nodes of level L over all instances (L < maxd)
   int has_und;
   std::vector<uint64_t> out_offsets;  // count + 1
   // device memory owned by the plan
   BInst* inst;
   uint64_t *chunk_cnt, *tile_tmp, *tile_cnt, *tile_off;
+  uint64_t* lvl_base;  // level_nodes.size() rows of count + 1 (batch_level_bases)
   TileDesc<BatchCtx>* desc;
   unsigned long long *big, *nbig;
   uint32_t* pairs_buf;
@@ -576,8 +610,16 @@ struct BatchPlan {
     uint64_t n, m, pair_base, out_base;
   };
   std::vector<Big> bigs;
-  void* big_arena = nullptr;
+  void* big_arena = nullptr;  // big_lanes areas of big_arena_bytes
   size_t big_arena_bytes = 0;
+  // the big instances run on big_lanes streams forked from the caller's
+  // stream and joined back (capturable): big k on lane big_lane[k], chosen
+  // largest first onto the least loaded lane; one lane is the caller's stream
+  static constexpr int BIG_LANES = 4;
+  int big_lanes = 1;
+  std::vector<int> big_lane;
+  cudaStream_t big_s[BIG_LANES] = {};
+  cudaEvent_t big_ev[BIG_LANES + 1] = {};
   // launch shapes chosen by kg_batch_tune (they do not change the output)
   unsigned tree_threads = 256;
   unsigned tiles_per_cta = 1;
@@ -599,6 +641,7 @@ static bool plan_carve(BatchPlan& bp, Workspace& ws) {
   bp.tile_tmp = ws.alloc<uint64_t>(tiles);
   bp.tile_cnt = ws.alloc<uint64_t>(tiles);
   bp.tile_off = ws.alloc<uint64_t>(tiles + 1);
+  bp.lvl_base = ws.alloc<uint64_t>(bp.level_nodes.size() * (count + 1));
   bp.desc = ws.alloc<TileDesc<BatchCtx>>(tiles);
   bp.big = ws.alloc<unsigned long long>(tiles);
   bp.nbig = ws.alloc<unsigned long long>(1);
@@ -620,8 +663,8 @@ static bool plan_carve(BatchPlan& bp, Workspace& ws) {
   bp.big_arena_bytes = 0;
   bp.big_arena = nullptr;
   if (need) {
-    bp.big_arena_bytes = need;
-    bp.big_arena = ws.alloc<unsigned char>(bp.big_arena_bytes);
+    bp.big_arena_bytes = piece(need);
+    bp.big_arena = ws.alloc<unsigned char>(bp.big_arena_bytes * uint64_t(bp.big_lanes));
   }
   return ws.ok();
 }
@@ -634,7 +677,8 @@ int batch_layout(const BatchSpec* specs, uint32_t count, std::vector<BInst>& tab
   bp.count = count;
   bp.out_offsets.assign(count + 1, 0);
   bp.bigs.clear();
-  uint64_t chunks = 0, tiles = 0, samples = 0, pairs = 0, verts = 0, entries = 0;
+  bp.level_nodes.clear();
+  uint64_t chunks = 0, tiles = 0, samples = 0, spairs = 0, bpairs = 0, verts = 0, entries = 0;
   for (uint32_t i = 0; i < count; ++i) {
     const BatchSpec& q = specs[i];
     BInst& I = tab[i];
@@ -670,33 +714,59 @@ int batch_layout(const BatchSpec* specs, uint32_t count, std::vector<BInst>& tab
     I.chunk_base = chunks;
     I.tile_base = tiles;
     I.sample_base = samples;
-    I.pair_base = pairs;
+    I.big = (I.undirected && q.m >= BIG_PAIRS) ? 1u : 0u;
+    I.spair_base = spairs;
+    I.pair_base = I.big ? bpairs : spairs;  // a big one's is moved past the small pairs below
     I.vert_base = verts;
     I.out_base = entries;
-    I.big = (I.undirected && q.m >= BIG_PAIRS) ? 1u : 0u;
     I.pad_ = 0;
     I.pad2_ = 0;
-    if (I.big) bp.bigs.push_back({q.n, q.m, pairs, entries});
+    if (I.big) bp.bigs.push_back({q.n, q.m, bpairs, entries});
     bp.out_offsets[i] = entries;
     chunks += I.C;
     tiles += I.C << I.d;
     samples += q.m;
-    if (I.undirected) {
-      pairs += q.m;
+    if (bp.level_nodes.size() < size_t(I.d)) bp.level_nodes.resize(size_t(I.d), 0);
+    for (int L = 0; L < I.d; ++L) bp.level_nodes[L] += I.C << L;
+    if (I.big) {
+      bpairs += q.m;
+      entries += 2 * q.m;
+    } else if (I.undirected) {
+      spairs += q.m;
       verts += q.n;
       entries += 2 * q.m;
     } else {
       entries += q.m;
     }
   }
+  for (BInst& I : tab)
+    if (I.big) I.pair_base += spairs;
+  for (auto& g : bp.bigs) g.pair_base += spairs;
+  // lanes of the big instances: largest first onto the least loaded lane
+  bp.big_lanes = int(std::min<size_t>(bp.bigs.size(), BatchPlan::BIG_LANES));
+  if (bp.big_lanes < 1) bp.big_lanes = 1;
+  bp.big_lane.assign(bp.bigs.size(), 0);
+  {
+    std::vector<size_t> order(bp.bigs.size());
+    for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t b) { return bp.bigs[a].m > bp.bigs[b].m; });
+    std::vector<uint64_t> load(size_t(bp.big_lanes), 0);
+    for (size_t k : order) {
+      const int l = int(std::min_element(load.begin(), load.end()) - load.begin());
+      bp.big_lane[k] = l;
+      load[size_t(l)] += bp.bigs[k].m;
+    }
+  }
   bp.out_offsets[count] = entries;
   bp.chunks = chunks;
   bp.tiles = tiles;
   bp.samples = samples;
-  bp.pairs = pairs;
+  bp.pairs = spairs + bpairs;
+  bp.spairs = spairs;
   bp.verts = verts;
   bp.entries = entries;
-  bp.has_und = pairs > 0;
+  bp.has_und = spairs > 0;
   return ST_OK;
 }
 
@@ -707,15 +777,29 @@ size_t batch_plan_bytes(BatchPlan& bp) {
   return meas.used();
 }
 
+static int batch_assemble_small(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream_t s,
+                                int* err);
+
 static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream_t s) {
   int* err = device_error_word();
   if (!err) return ST_CUDA;
   const uint32_t count = bp->count;
   {
     ProfScope ps(PROF_CHUNK_TREE, s);
-    batch_trees<<<count, bp->tree_threads, 0, s>>>(bp->inst, bp->chunk_cnt, bp->tile_tmp,
-                                                   bp->tile_cnt, err);
+    batch_trees<<<count, bp->tree_threads, 0, s>>>(bp->inst, bp->chunk_cnt, bp->tile_cnt, err);
     if (launch_ok()) return ST_CUDA;
+  }
+  if (!bp->level_nodes.empty()) {
+    ProfScope ps(PROF_TILE_TREE, s);
+    batch_level_bases<<<unsigned(bp->level_nodes.size()), 1024, 0, s>>>(bp->inst, count,
+                                                                         bp->lvl_base);
+    if (launch_ok()) return ST_CUDA;
+    for (size_t L = 0; L < bp->level_nodes.size(); ++L) {
+      batch_tile_level<<<grid_for(bp->level_nodes[L], 256, sm_count() * 8), 256, 0, s>>>(
+          bp->inst, count, int(L), bp->lvl_base + L * (uint64_t(count) + 1), bp->chunk_cnt,
+          bp->tile_tmp, bp->tile_cnt, err);
+      if (launch_ok()) return ST_CUDA;
+    }
   }
   int st = scan_exclusive_u64(bp->tile_cnt, bp->tile_off, bp->tiles, bp->scan_t, s);
   if (st) return st;
@@ -743,8 +827,67 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
         bp->nbig);
     if (launch_ok()) return ST_CUDA;
   }
-  if (!bp->has_und) return ST_OK;
-  const uint64_t V = bp->verts, Mp = bp->pairs;
+  if (bp->has_und) {
+    st = batch_assemble_small(bp, out, cap, s, err);
+    if (st) return st;
+  }
+  if (bp->bigs.empty()) return ST_OK;
+  // the big undirected instances, each by the per-instance assembly, on
+  // big_lanes streams (lane 0 is s); a lane's scratch area is reused in its
+  // stream order
+  const int nl = bp->big_lanes;
+  cudaStream_t lane_s[BatchPlan::BIG_LANES];
+  lane_s[0] = s;
+  for (int l = 1; l < nl; ++l) lane_s[l] = bp->big_s[l];
+  bool forked = false;
+  if (nl > 1) {
+    if (cudaEventRecord(bp->big_ev[0], s) != cudaSuccess) return ST_CUDA;
+    for (int l = 1; l < nl; ++l)
+      if (cudaStreamWaitEvent(lane_s[l], bp->big_ev[0], 0) != cudaSuccess) return ST_CUDA;
+    forked = true;
+  }
+  for (size_t k = 0; k < bp->bigs.size() && st == ST_OK; ++k) {
+    const auto& g = bp->bigs[k];
+    const int l = bp->big_lane[k];
+    Workspace wb(lane_s[l], static_cast<unsigned char*>(bp->big_arena) + uint64_t(l) * bp->big_arena_bytes,
+                 bp->big_arena_bytes);
+    st = assemble<uint32_t>(bp->pairs_buf + 2 * g.pair_base, nullptr, g.m, g.n,
+                            out + 2 * g.out_base, 2 * g.m, wb, lane_s[l], err);
+  }
+  // every forked lane joins back, also after an error (a capture must end joined)
+  if (forked)
+    for (int l = 1; l < nl; ++l)
+      if (cudaEventRecord(bp->big_ev[l], lane_s[l]) != cudaSuccess ||
+          cudaStreamWaitEvent(s, bp->big_ev[l], 0) != cudaSuccess)
+        st = ST_CUDA;
+  return st;
+}
+
+// Streams and events of the big instances' lanes (lanes 1 .. big_lanes - 1).
+static bool big_lanes_create(BatchPlan& bp) {
+  for (int l = 1; l < bp.big_lanes; ++l)
+    if (cudaStreamCreateWithFlags(&bp.big_s[l], cudaStreamNonBlocking) != cudaSuccess) return false;
+  for (int l = 0; l < bp.big_lanes; ++l)
+    if (cudaEventCreateWithFlags(&bp.big_ev[l], cudaEventDisableTiming) != cudaSuccess) return false;
+  return true;
+}
+
+static void big_lanes_destroy(BatchPlan& bp) {
+  for (int l = 0; l < BatchPlan::BIG_LANES; ++l) {
+    if (bp.big_s[l]) cudaStreamDestroy(bp.big_s[l]);
+    if (bp.big_ev[l]) cudaEventDestroy(bp.big_ev[l]);
+    bp.big_s[l] = nullptr;
+    bp.big_ev[l] = nullptr;
+  }
+}
+
+// Undirected assembly of the small instances: one pass over all of them (their
+// pairs are the first spairs of the pair buffer, their vertex ranges concatenated).
+static int batch_assemble_small(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream_t s,
+                                int* err) {
+  const uint32_t count = bp->count;
+  const uint64_t V = bp->verts, Mp = bp->spairs;
+  int st = ST_OK;
   if (cudaMemsetAsync(bp->deg, 0, V * 8, s) != cudaSuccess ||
       cudaMemsetAsync(bp->nlong, 0, 8, s) != cudaSuccess)
     return ST_CUDA;
@@ -783,15 +926,7 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
                                                 bp->nlong);
     if (launch_ok()) return ST_CUDA;
   }
-  // the big undirected instances, one after the other, each by the
-  // per-instance assembly over its slices (the scratch is reused in stream order)
-  for (const auto& g : bp->bigs) {
-    Workspace wb(s, bp->big_arena, bp->big_arena_bytes);
-    st = assemble<uint32_t>(bp->pairs_buf + 2 * g.pair_base, nullptr, g.m, g.n,
-                            out + 2 * g.out_base, 2 * g.m, wb, s, err);
-    if (st) return st;
-  }
-  return ST_OK;
+  return st;
 }
 
 struct BatchGroup {
@@ -808,7 +943,8 @@ int batch_group_prepare(const BatchSpec* specs, uint32_t count, BatchGroup** out
     delete g;
     return st;
   }
-  if (cudaGetDevice(&g->plan.device) != cudaSuccess) {
+  if (cudaGetDevice(&g->plan.device) != cudaSuccess || !big_lanes_create(g->plan)) {
+    big_lanes_destroy(g->plan);
     delete g;
     return ST_CUDA;
   }
@@ -846,7 +982,11 @@ const uint64_t* batch_group_digests(const BatchGroup* g) {
   return reinterpret_cast<const uint64_t*>(g->dig);
 }
 
-void batch_group_free(BatchGroup* g) { delete g; }
+void batch_group_free(BatchGroup* g) {
+  if (!g) return;
+  big_lanes_destroy(g->plan);
+  delete g;
+}
 
 }  // namespace kg
 
@@ -875,13 +1015,15 @@ kg_status kg_batch_create(const kg_instance* h_inst, uint32_t count, int id_byte
     delete b;
     return kg_status(st);
   }
-  if (cudaGetDevice(&bp.device) != cudaSuccess) {
+  if (cudaGetDevice(&bp.device) != cudaSuccess || !big_lanes_create(bp)) {
+    big_lanes_destroy(bp);
     delete b;
     return KG_ERR_CUDA;
   }
   // the plan's device memory: one allocation, carved as the measuring pass counted
   const size_t bytes = batch_plan_bytes(bp);
   if (cudaMalloc(&bp.mem, bytes ? bytes : 256) != cudaSuccess) {
+    big_lanes_destroy(bp);
     delete b;
     return KG_ERR_CUDA;
   }
@@ -889,6 +1031,7 @@ kg_status kg_batch_create(const kg_instance* h_inst, uint32_t count, int id_byte
   if (!plan_carve(bp, ws) ||
       cudaMemcpy(bp.inst, tab.data(), sizeof(BInst) * count, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(bp.mem);
+    big_lanes_destroy(bp);
     delete b;
     return KG_ERR_CUDA;
   }
@@ -899,6 +1042,7 @@ kg_status kg_batch_create(const kg_instance* h_inst, uint32_t count, int id_byte
 kg_status kg_batch_destroy(kg_batch* b) {
   if (!b) return KG_OK;
   if (b->plan.mem) cudaFree(b->plan.mem);
+  big_lanes_destroy(b->plan);
   delete b;
   return KG_OK;
 }
