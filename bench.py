@@ -29,11 +29,11 @@ N_VERT, M_EDGES, P_CHUNKS, SEED = 1 << 36, 1 << 33, 1 << 16, 1
 SLABS = 16
 CHUNKS_PER_SLAB = P_CHUNKS // SLABS
 SLAB_CAP = (1 << 29) + (1 << 21)  # edges per slab buffer (mean 2^29, sd ~2^14.5)
-# DRAM bytes (read + write) per edge of the leaf kernel, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum) of its launch on chunks
-# [0, 256) of this workload (python bench.py --profile-chunks 256):
-# 480,359,936 B / 33,550,402 edges; scaled to a slab launch by its edges.
-LEAF_TRAFFIC_PER_EDGE = (476915968 + 3443968) / 33550402
+# DRAM bytes (read + write) per edge of the leaf kernel (leaf_sparse_kernel),
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of its
+# launch on chunks [0, 256) of this workload (python bench.py --profile-chunks
+# 256): 495,079,424 B / 33,550,402 edges; scaled to a slab launch by its edges.
+LEAF_TRAFFIC_PER_EDGE = (489387264 + 5692160) / 33550402
 ID_BYTES = 8
 WORKLOAD = "directed G(n,m): n=2^36, m=2^33, 2^16 chunks, uint64 ids, 16 slabs of 8 GiB, per-chunk digest + out-degree histogram"
 METRIC = "edges/s (directed G(n,m), n=2^36, m=2^33, 2^16 chunks, uint64 ids, on-device digest)"
@@ -775,7 +775,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": LEAF_TRAFFIC_PER_EDGE * M_EDGES / SLABS,
-                     "kernel": "leaf_fast_kernel (Floyd draws, shared-memory sort, emit, digest)",
+                     "kernel": "leaf_sparse_kernel (Floyd draws, shared-memory bucket sort, emit, digest)",
                      "peak_kind": f"{peak_kind} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                      "write_peak_GBps": wpeak, "frac_of_write_peak": achieved / wpeak,
                      "write_peak_kind": "measured: the library's own 16-byte store kernel "

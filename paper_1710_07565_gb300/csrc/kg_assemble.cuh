@@ -21,6 +21,13 @@ inline bool asm_shape(uint64_t nrows, uint64_t entries, int& bsh, uint32_t& nb) 
   bsh = 0;
   while ((1u << (bsh + 1)) <= ASM_BR_MAX && double(1u << (bsh + 1)) * avg <= double(ASM_TARGET))
     ++bsh;
+  // too many buckets for the histogram: wider buckets while they expect at
+  // most three quarters of what shared memory holds (a window of 2^24 rows at
+  // 2.02 entries per row takes 2^14 buckets of 2^10 rows, ~2070 entries each)
+  while (((nrows + (uint64_t(1) << bsh) - 1) >> bsh) > ASM_NB_MAX &&
+         (1u << (bsh + 1)) <= ASM_BR_MAX &&
+         double(1u << (bsh + 1)) * avg <= 0.75 * double(ASM_CAP))
+    ++bsh;
   const uint64_t b = (nrows + (uint64_t(1) << bsh) - 1) >> bsh;
   nb = uint32_t(b < ASM_NB_MAX ? b : ASM_NB_MAX);
   // measured on GB300: the buckets win on windows of 2^22 rows and more and

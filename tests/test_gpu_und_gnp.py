@@ -294,3 +294,22 @@ def test_bucketed_assembly_whole_graph(kg, orc):
     gu, gv = edges_np(t, 4)
     ou, ov = orc.gnm_undirected(n, m, 3, P)
     assert_same_edges(gu, gv, ou, ov, "bucketed assembly")
+
+
+def test_bucketed_assembly_widened_buckets(kg, orc):
+    """A row window of 2^24 rows (n = 2^26, 64 row blocks, blocks [8, 24)) whose
+    caller-given capacity allows 2.2 entries per row: at the target bucket
+    width that needs 2^15 buckets, more than the shared-memory histogram holds,
+    so the assembly widens them to 2^10 rows (2^14 buckets); the window's rows,
+    digests and degree histograms equal the oracle's."""
+    n, m, P, seed, b0, b1 = 1 << 26, 1 << 25, 64, 11, 8, 24
+    cap = int(2.2 * (1 << 24))
+    t, dig, hist = _rows(kg, n, m, seed, P, b0, b1, 4, cap)
+    gu, gv = edges_np(t, 4)
+    ou, ov = orc.gnm_undirected_rows(n, m, seed, P, b0, b1, cap_hint=cap)
+    assert_same_edges(gu, gv, ou, ov, "widened buckets")
+    for b in range(b0, b1):
+        lo, hi = b * n // P, (b + 1) * n // P
+        sel = (ou >= lo) & (ou < hi)
+        assert int(dig[b - b0]) == orc.edge_checksum(ou[sel], ov[sel])
+        assert np.array_equal(hist[b - b0], orc.outdegree_hist(ou[sel], lo, hi))
