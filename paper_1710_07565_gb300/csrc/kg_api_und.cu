@@ -172,17 +172,22 @@ static int gnm_undirected_rows_impl(const UndParams& up, uint64_t seed, uint32_t
   const uint64_t row_lo = rb(b0), nrows = rb(b1) - row_lo;
   uint64_t* rowptr = nullptr;
   Id* out = static_cast<Id*>(d_out);
-  if ((st = assemble<Id>(pairs, npairs, 0, up.n, out, cap, ws, s, err, row_lo, nrows, &rowptr,
-                         cap)))
-    return st;
-  if (d_entries && cudaMemcpyAsync(d_entries, rowptr + nrows, 8, cudaMemcpyDeviceToDevice, s) !=
-                       cudaSuccess)
-    return ST_CUDA;
   if (d_digest || d_hist) {
     const uint64_t nb = b1 - b0;
     if ((d_digest && cudaMemsetAsync(d_digest, 0, nb * 8, s) != cudaSuccess) ||
         (d_hist && cudaMemsetAsync(d_hist, 0, nb * 65 * 8, s) != cudaSuccess))
       return ST_CUDA;
+  }
+  const AsmDigest dig{rb, b0, reinterpret_cast<unsigned long long*>(d_digest),
+                      reinterpret_cast<unsigned long long*>(d_hist)};
+  bool digested = false;
+  if ((st = assemble<Id>(pairs, npairs, 0, up.n, out, cap, ws, s, err, row_lo, nrows, &rowptr,
+                         cap, (d_digest || d_hist) ? &dig : nullptr, &digested)))
+    return st;
+  if (d_entries && cudaMemcpyAsync(d_entries, rowptr + nrows, 8, cudaMemcpyDeviceToDevice, s) !=
+                       cudaSuccess)
+    return ST_CUDA;
+  if ((d_digest || d_hist) && !digested) {
     ProfScope ps(PROF_DIGEST, s);
     und_block_digest<Id><<<grid_for(nrows, unsigned(DIGEST_SEG), sm_count() * 16), 256, 0, s>>>(
         out, rowptr, row_lo, nrows, rb, b0, reinterpret_cast<unsigned long long*>(d_digest),

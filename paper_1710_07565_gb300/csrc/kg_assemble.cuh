@@ -47,7 +47,9 @@ struct AsmScratch {
   uint32_t nb = 0;
   uint64_t* rowptr = nullptr;  // nrows + 1 row offsets (both paths)
   // bucketed path
-  unsigned long long *bcnt = nullptr, *bcur = nullptr, *big = nullptr, *nbig = nullptr;
+  unsigned long long *bcnt = nullptr, *big = nullptr, *nbig = nullptr;
+  uint32_t* blk = nullptr;  // G rows of nb per-block bucket counts, then offsets
+  uint32_t G = 0;           // blocks of the count and scatter kernels
   uint64_t* boff = nullptr;
   // atomic path
   unsigned long long *deg = nullptr, *cursor = nullptr, *long_rows = nullptr, *nlong = nullptr;
@@ -58,9 +60,10 @@ struct AsmScratch {
     buckets = nrows > 0 && asm_shape(nrows, expect, bsh, nb);
     rowptr = ws.alloc<uint64_t>(nrows + 1);
     if (buckets) {
+      G = uint32_t(sm_count() * 2);
       bcnt = ws.alloc<unsigned long long>(nb);
       boff = ws.alloc<uint64_t>(uint64_t(nb) + 1);
-      bcur = ws.alloc<unsigned long long>(nb);
+      blk = ws.alloc<uint32_t>(uint64_t(G) * nb);
       big = ws.alloc<unsigned long long>(nb);
       nbig = ws.alloc<unsigned long long>(1);
       if (!scan_scratch(nb, ws, scan)) return false;
@@ -94,15 +97,12 @@ inline uint64_t assemble_scratch_bytes(uint64_t nrows, uint64_t expect) {
 template <class Id>
 inline int assemble_buckets(const Id* pairs, const uint64_t* npairs_dev, uint64_t npairs_host,
                             Id* out, uint64_t cap, const AsmScratch& sc, cudaStream_t s, int* err,
-                            uint64_t row_lo, uint64_t nrows) {
+                            uint64_t row_lo, uint64_t nrows, const AsmDigest& dig) {
   const int bsh = sc.bsh;
   const uint32_t nb = sc.nb;
-  if (cudaMemsetAsync(sc.bcnt, 0, uint64_t(nb) * 8, s) != cudaSuccess ||
-      cudaMemsetAsync(sc.bcur, 0, uint64_t(nb) * 8, s) != cudaSuccess ||
-      cudaMemsetAsync(sc.nbig, 0, 8, s) != cudaSuccess)
-    return ST_CUDA;
+  if (cudaMemsetAsync(sc.nbig, 0, 8, s) != cudaSuccess) return ST_CUDA;
   const size_t hsm = size_t(nb) * 4;
-  const unsigned G = unsigned(sm_count() * 2);
+  const unsigned G = sc.G;  // the count and scatter kernels split the pairs alike
   static_assert(size_t(ASM_NB_MAX) * 4 <= 64 * 1024, "histogram in shared memory");
   if (cudaFuncSetAttribute(asm_bucket_count<Id>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(ASM_NB_MAX * 4)) != cudaSuccess ||
@@ -114,7 +114,12 @@ inline int assemble_buckets(const Id* pairs, const uint64_t* npairs_dev, uint64_
   {
     ProfScope ps(PROF_ASSEMBLY, s);
     asm_bucket_count<Id><<<G, ASM_THREADS, hsm, s>>>(pairs, npairs_dev, npairs_host, row_lo, nrows,
-                                                     bsh, nb, sc.bcnt);
+                                                     bsh, nb, sc.blk);
+    if (launch_ok()) return ST_CUDA;
+  }
+  {
+    ProfScope ps(PROF_ASSEMBLY, s);
+    asm_bucket_colscan<<<(nb + 63) / 64, 64, 0, s>>>(sc.blk, G, nb, sc.bcnt);
     if (launch_ok()) return ST_CUDA;
   }
   int st = scan_exclusive_u64(reinterpret_cast<const uint64_t*>(sc.bcnt), sc.boff, nb, sc.scan, s);
@@ -122,20 +127,20 @@ inline int assemble_buckets(const Id* pairs, const uint64_t* npairs_dev, uint64_
   {
     ProfScope ps(PROF_ASSEMBLY, s);
     asm_bucket_scatter<Id><<<G, ASM_THREADS, hsm, s>>>(pairs, npairs_dev, npairs_host, row_lo,
-                                                       nrows, bsh, nb, sc.boff, sc.bcur, out, cap,
+                                                       nrows, bsh, nb, sc.boff, sc.blk, out, cap,
                                                        err);
     if (launch_ok()) return ST_CUDA;
   }
   {
     ProfScope ps(PROF_ASSEMBLY, s);
     asm_bucket_sort<Id><<<grid_for(nb, 1, sm_count() * 4), ASM_THREADS, sizeof(AsmSmem), s>>>(
-        out, sc.boff, row_lo, nrows, bsh, nb, cap, sc.rowptr, sc.big, sc.nbig);
+        out, sc.boff, row_lo, nrows, bsh, nb, cap, sc.rowptr, sc.big, sc.nbig, dig);
     if (launch_ok()) return ST_CUDA;
   }
   {
     ProfScope ps(PROF_ASSEMBLY, s);
     asm_bucket_sort_global<Id><<<sm_count(), ASM_THREADS, 0, s>>>(out, sc.boff, row_lo, nrows, bsh,
-                                                                   sc.rowptr, sc.big, sc.nbig);
+                                                                   sc.rowptr, sc.big, sc.nbig, dig);
     if (launch_ok()) return ST_CUDA;
   }
   // the window's last offset: its entry count
@@ -149,13 +154,22 @@ template <class Id>
 inline int assemble(const Id* pairs, const uint64_t* npairs_dev, uint64_t npairs_host, uint64_t n,
                     Id* out, uint64_t cap, Workspace& ws, cudaStream_t s, int* err,
                     uint64_t row_lo = 0, uint64_t nrows = ~uint64_t(0),
-                    uint64_t** rowptr_out = nullptr, uint64_t work_bound = 0) {
+                    uint64_t** rowptr_out = nullptr, uint64_t work_bound = 0,
+                    const AsmDigest* dig = nullptr, bool* digested = nullptr) {
   if (nrows == ~uint64_t(0)) nrows = n;
   AsmScratch sc;
   if (!sc.carve(nrows, asm_expect(npairs_dev, npairs_host, cap), ws)) return ST_CUDA;
   if (rowptr_out) *rowptr_out = sc.rowptr;
-  if (sc.buckets)
-    return assemble_buckets<Id>(pairs, npairs_dev, npairs_host, out, cap, sc, s, err, row_lo, nrows);
+  if (digested) *digested = false;
+  if (sc.buckets) {
+    // the bucketed path also makes the window's per-row-block digests and
+    // degree histograms (zeroed by the caller) while the entries are on chip
+    AsmDigest none{};
+    const AsmDigest& dd = dig ? *dig : none;
+    if (digested) *digested = dig != nullptr;
+    return assemble_buckets<Id>(pairs, npairs_dev, npairs_host, out, cap, sc, s, err, row_lo, nrows,
+                                dd);
+  }
   uint64_t* rowptr = sc.rowptr;
   unsigned long long *deg = sc.deg, *cursor = sc.cursor, *long_rows = sc.long_rows,
                      *nlong = sc.nlong;

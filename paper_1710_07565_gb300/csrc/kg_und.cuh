@@ -467,10 +467,11 @@ namespace kg {
 // ---------------------------------------------------------------- bucketed assembly
 // The window's rows are cut into buckets of 2^bsh consecutive rows, sized so
 // that a bucket holds about ASM_TARGET entries.  (1) Every block histograms
-// its contiguous share of the pairs by bucket in shared memory and adds the
-// counts to the global ones; (2) a scan gives every bucket its final range of
-// the output; (3) every block claims, per bucket, a sub-range for its share
-// (one atomic per bucket and block) and scatters its entries there; (4) one
+// its contiguous share of the pairs by bucket in shared memory and stores
+// its histogram; (2) per bucket, the blocks' counts become the blocks'
+// offsets inside the bucket and a scan of the buckets' totals gives every
+// bucket its final range of the output; (3) every block scatters its share's
+// entries to its sub-range of each bucket; (4) one
 // CTA per bucket loads the bucket's entries into shared memory, sorts them
 // by row (counting sort) and each row by column, writes them back in order
 // and fills the rows' offsets.  Buckets larger than shared memory are sorted
@@ -493,11 +494,13 @@ __device__ __forceinline__ void asm_share(uint64_t np, uint32_t blk, uint32_t nb
   if (i0 > np) i0 = np;
 }
 
+// (1) per block: the bucket histogram of its share, stored as row blockIdx.x
+// of blk (nb counters per block, no atomics outside shared memory)
 template <class Id>
 __global__ void __launch_bounds__(ASM_THREADS)
     asm_bucket_count(const Id* __restrict__ pairs, const uint64_t* __restrict__ npairs_dev,
                      uint64_t npairs_host, uint64_t row_lo, uint64_t nrows, int bsh, uint32_t nb,
-                     unsigned long long* __restrict__ bcnt) {
+                     uint32_t* __restrict__ blk) {
   extern __shared__ uint32_t hcnt[];
   for (uint32_t i = threadIdx.x; i < nb; i += ASM_THREADS) hcnt[i] = 0;
   __syncthreads();
@@ -510,33 +513,48 @@ __global__ void __launch_bounds__(ASM_THREADS)
     if (v - row_lo < nrows) atomicAdd(&hcnt[(v - row_lo) >> bsh], 1u);
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < nb; i += ASM_THREADS)
-    if (hcnt[i]) atomicAdd(&bcnt[i], (unsigned long long)hcnt[i]);
+  uint32_t* row = blk + uint64_t(blockIdx.x) * nb;
+  for (uint32_t i = threadIdx.x; i < nb; i += ASM_THREADS) row[i] = hcnt[i];
 }
 
-// bcur[b]: entries of bucket b claimed so far (zero before the launch)
+// Per bucket b (one thread each): the counts of the G blocks become each
+// block's offset inside the bucket (exclusive prefix over the blocks, in
+// block order), and bcnt[b] the bucket's total.
+static __global__ void __launch_bounds__(64)
+    asm_bucket_colscan(uint32_t* __restrict__ blk, uint32_t G, uint32_t nb,
+                       unsigned long long* __restrict__ bcnt) {
+  const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= nb) return;
+  uint32_t run = 0;
+  constexpr uint32_t U = 16;  // loads in flight before the dependent stores
+  for (uint32_t g0 = 0; g0 < G; g0 += U) {
+    uint32_t c[U];
+#pragma unroll
+    for (uint32_t j = 0; j < U; ++j) c[j] = g0 + j < G ? blk[uint64_t(g0 + j) * nb + b] : 0u;
+#pragma unroll
+    for (uint32_t j = 0; j < U; ++j)
+      if (g0 + j < G) {
+        blk[uint64_t(g0 + j) * nb + b] = run;
+        run += c[j];
+      }
+  }
+  bcnt[b] = run;
+}
+
+// (3) per block, the same share as in (1): every entry goes to its bucket's
+// range at the block's offset in it (blk after asm_bucket_colscan)
 template <class Id>
 __global__ void __launch_bounds__(ASM_THREADS)
     asm_bucket_scatter(const Id* __restrict__ pairs, const uint64_t* __restrict__ npairs_dev,
                        uint64_t npairs_host, uint64_t row_lo, uint64_t nrows, int bsh, uint32_t nb,
-                       const uint64_t* __restrict__ boff, unsigned long long* __restrict__ bcur,
+                       const uint64_t* __restrict__ boff, const uint32_t* __restrict__ blk,
                        Id* __restrict__ out, uint64_t cap, int* err) {
-  extern __shared__ uint32_t hcur[];  // per bucket: this block's count, then its next slot
-  for (uint32_t i = threadIdx.x; i < nb; i += ASM_THREADS) hcur[i] = 0;
+  extern __shared__ uint32_t hcur[];  // per bucket: this block's next slot in it
+  const uint32_t* row = blk + uint64_t(blockIdx.x) * nb;
+  for (uint32_t i = threadIdx.x; i < nb; i += ASM_THREADS) hcur[i] = row[i];
   __syncthreads();
   uint64_t i0, i1;
   asm_share(npairs_dev ? *npairs_dev : npairs_host, blockIdx.x, gridDim.x, i0, i1);
-  for (uint64_t i = i0 + threadIdx.x; i < i1; i += ASM_THREADS) {
-    uint64_t u, v;
-    load_pair(pairs, i, u, v);
-    if (u - row_lo < nrows) atomicAdd(&hcur[(u - row_lo) >> bsh], 1u);
-    if (v - row_lo < nrows) atomicAdd(&hcur[(v - row_lo) >> bsh], 1u);
-  }
-  __syncthreads();
-  // the block's sub-range of every bucket, relative to the bucket's start
-  for (uint32_t i = threadIdx.x; i < nb; i += ASM_THREADS)
-    if (hcur[i]) hcur[i] = uint32_t(atomicAdd(&bcur[i], (unsigned long long)hcur[i]));
-  __syncthreads();
   for (uint64_t i = i0 + threadIdx.x; i < i1; i += ASM_THREADS) {
     uint64_t u, v;
     load_pair(pairs, i, u, v);
@@ -558,6 +576,17 @@ __global__ void __launch_bounds__(ASM_THREADS)
     }
   }
 }
+
+// Per-row-block digest (sum of edge_hash over the entries) and out-degree
+// histogram (65 bins, the last for 64 and more) of an assembly window, made
+// while the entries are in shared memory; row block b of the window is
+// b - b_lo.  Both pointers null: none.
+struct AsmDigest {
+  RowBounds rb;
+  uint64_t b_lo;
+  unsigned long long* digest;
+  unsigned long long* hist;
+};
 
 struct AsmSmem {
   uint64_t key[ASM_CAP];   // (row in bucket) << 48 | column, as loaded
@@ -663,9 +692,12 @@ __global__ void __launch_bounds__(ASM_THREADS)
     asm_bucket_sort(Id* __restrict__ out, const uint64_t* __restrict__ boff, uint64_t row_lo,
                     uint64_t nrows, int bsh, uint32_t nb, uint64_t cap,
                     uint64_t* __restrict__ rowptr, unsigned long long* __restrict__ big,
-                    unsigned long long* __restrict__ nbig) {
+                    unsigned long long* __restrict__ nbig, AsmDigest dig) {
   extern __shared__ __align__(16) unsigned char asm_raw[];
   AsmSmem& sm = *reinterpret_cast<AsmSmem*>(asm_raw);
+  __shared__ unsigned long long sh_dig;
+  __shared__ uint32_t sh_hist[65];
+  const bool dg = dig.digest != nullptr || dig.hist != nullptr;
   for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
     const uint64_t e0 = boff[b], e1 = boff[b + 1];
     const uint64_t r0 = uint64_t(b) << bsh;
@@ -683,6 +715,8 @@ __global__ void __launch_bounds__(ASM_THREADS)
     const uint32_t c = uint32_t(c64);
     for (uint32_t r = threadIdx.x; r <= nr; r += ASM_THREADS) sm.rc[r] = 0;
     if (threadIdx.x == 0) sm.nlong = 0;
+    if (threadIdx.x < 65) sh_hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0) sh_dig = 0;
     __syncthreads();
     for (uint32_t i = threadIdx.x; i < c; i += ASM_THREADS) {
       uint64_t u, v;
@@ -746,11 +780,60 @@ __global__ void __launch_bounds__(ASM_THREADS)
       const uint32_t s1 = sm.rc[r], s0 = r ? sm.rc[r - 1] : 0;
       asm_block_sort(sm.sorted + s0, s1 - s0);
     }
+    // the bucket's rows lie in one row block (almost always) or straddle several
+    uint64_t bA = 0;
+    bool one = true;
+    if (dg) {
+      bA = block_of_row(dig.rb, row_lo + r0);
+      one = block_of_row(dig.rb, row_lo + r0 + nr - 1) == bA;
+    }
+    unsigned long long ds = 0;
     for (uint32_t i = threadIdx.x; i < c; i += ASM_THREADS) {
       const uint64_t k = sm.sorted[i];
-      store_pair(out, e0 + i, row_lo + r0 + (k >> 48), k & ((uint64_t(1) << 48) - 1));
+      const uint64_t u = row_lo + r0 + (k >> 48), v = k & ((uint64_t(1) << 48) - 1);
+      store_pair(out, e0 + i, u, v);
+      if (dig.digest) {
+        const unsigned long long h = edge_hash(u, v);
+        if (one)
+          ds += h;
+        else
+          atomicAdd(&dig.digest[block_of_row(dig.rb, u) - dig.b_lo], h);
+      }
+    }
+    if (dg) {
+      const unsigned lane = threadIdx.x & 31;
+      if (dig.hist) {
+        // rc[r] is the end of row r: degrees 0..7 counted in registers and
+        // summed over the warp, longer ones in shared memory
+        uint32_t c8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (uint32_t r = threadIdx.x; r < nr; r += ASM_THREADS) {
+          const uint32_t deg = sm.rc[r] - (r ? sm.rc[r - 1] : 0u);
+          const uint32_t bin = deg < 64 ? deg : 64;
+          if (!one)
+            atomicAdd(&dig.hist[(block_of_row(dig.rb, row_lo + r0 + r) - dig.b_lo) * 65 + bin], 1ull);
+          else if (deg < 8)
+            ++c8[deg];
+          else
+            atomicAdd(&sh_hist[bin], 1u);
+        }
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+          const uint32_t t = __reduce_add_sync(0xffffffffu, c8[d]);
+          if (lane == 0 && t) atomicAdd(&sh_hist[d], t);
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ds += __shfl_xor_sync(0xffffffffu, ds, o);
+      if (lane == 0 && ds) atomicAdd(&sh_dig, ds);
     }
     __syncthreads();
+    // one atomic per bin and bucket (the same threads reset these at the next bucket)
+    if (dg && one) {
+      const uint64_t bi = bA - dig.b_lo;
+      if (dig.digest && threadIdx.x == 0 && sh_dig) atomicAdd(&dig.digest[bi], sh_dig);
+      if (dig.hist && threadIdx.x < 65 && sh_hist[threadIdx.x])
+        atomicAdd(&dig.hist[bi * 65 + threadIdx.x], (unsigned long long)sh_hist[threadIdx.x]);
+    }
   }
 }
 
@@ -763,7 +846,7 @@ __global__ void __launch_bounds__(ASM_THREADS)
                            uint64_t row_lo, uint64_t nrows, int bsh,
                            uint64_t* __restrict__ rowptr,
                            const unsigned long long* __restrict__ big,
-                           const unsigned long long* __restrict__ nbig) {
+                           const unsigned long long* __restrict__ nbig, AsmDigest dig) {
   const unsigned long long nb = *nbig;
   for (unsigned long long q = blockIdx.x; q < nb; q += gridDim.x) {
     const uint32_t b = uint32_t(big[q]);
@@ -829,6 +912,22 @@ __global__ void __launch_bounds__(ASM_THREADS)
       }
       rowptr[r0 + r] = e0 + a;
     }
+    __syncthreads();
+    // digest and degree histogram row by row (this path is rare: global atomics)
+    if (dig.digest || dig.hist)
+      for (uint64_t r = threadIdx.x; r < nr; r += ASM_THREADS) {
+        const uint64_t s0 = rowptr[r0 + r], s1 = r + 1 < nr ? rowptr[r0 + r + 1] : e0 + n;
+        const uint64_t row = row_lo + r0 + r;
+        const uint64_t bi = block_of_row(dig.rb, row) - dig.b_lo;
+        unsigned long long ds = 0;
+        for (uint64_t e = s0; e < s1; ++e) {
+          uint64_t u, v;
+          load_pair(out, e, u, v);
+          ds += edge_hash(u, v);
+        }
+        if (dig.digest && ds) atomicAdd(&dig.digest[bi], ds);
+        if (dig.hist) atomicAdd(&dig.hist[bi * 65 + (s1 - s0 < 64 ? s1 - s0 : 64)], 1ull);
+      }
     __syncthreads();
   }
 }
