@@ -635,6 +635,32 @@ def profile_rgg(kg, dim, lg):
     print(json.dumps({"profile_rgg": dim, "n": n, "entries": k}))
 
 
+def profile_und_rows(kg, ranges):
+    """Undirected G(n,m) at n = m = 2^32 (uint64 ids, 4096 x 4096 chunk
+    matrix): the chunk counts, then the first `ranges` row ranges of 16 row
+    blocks with per-block digests and degree histograms (the case of the
+    undirected launch list under profiles/)."""
+    import torch
+    n, m, P, seed, per = 1 << 32, 1 << 32, 4096, 1, 16
+    s = torch.cuda.current_stream().cuda_stream
+    counts = torch.zeros(P * (P + 1) // 2, dtype=torch.int64, device="cuda")
+    mean = (2 * m) // (P // per)
+    cap = mean + 64 * int(mean ** 0.5) + 4096
+    out = torch.empty((cap, 2), dtype=torch.int64, device="cuda")
+    ent = torch.zeros(ranges, dtype=torch.int64, device="cuda")
+    dig = torch.zeros(P, dtype=torch.int64, device="cuda")
+    hist = torch.zeros((P, 65), dtype=torch.int64, device="cuda")
+    kg.kg_gnm_undirected_chunk_counts(n, m, seed, P, counts.data_ptr(), s)
+    for r in range(ranges):
+        b0 = r * per
+        kg.kg_gnm_undirected_rows(n, m, seed, P, b0, b0 + per, counts.data_ptr(), 8,
+                                  out.data_ptr(), cap, ent.data_ptr() + 8 * r,
+                                  dig.data_ptr() + 8 * b0, hist.data_ptr() + 8 * 65 * b0, s)
+    torch.cuda.synchronize()
+    kg.check_device_error()
+    print(json.dumps({"profile_und_rows": ranges, "entries": int(ent.sum())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -651,6 +677,9 @@ def main():
     ap.add_argument("--profile-rgg", type=int, nargs=2, metavar=("DIM", "LOG2N"), default=None,
                     help="run only RGG(2^LOG2N, 16 neighbours) in DIM dimensions (count pass, "
                          "then two kg_rgg calls) and exit")
+    ap.add_argument("--profile-und-rows", type=int, default=0, metavar="RANGES",
+                    help="run only undirected G(n,m) at n = m = 2^32: the chunk counts and the "
+                         "first RANGES row ranges of 16 row blocks, and exit")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -669,6 +698,8 @@ def main():
         return profile_case(kg, args.profile_chunks)
     if args.profile_rgg:
         return profile_rgg(kg, *args.profile_rgg)
+    if args.profile_und_rows:
+        return profile_und_rows(kg, args.profile_und_rows)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
