@@ -60,7 +60,7 @@ struct AsmScratch {
     buckets = nrows > 0 && asm_shape(nrows, expect, bsh, nb);
     rowptr = ws.alloc<uint64_t>(nrows + 1);
     if (buckets) {
-      G = uint32_t(sm_count() * 2);
+      G = uint32_t(sm_count() * ASM_HIST_BLOCKS);
       bcnt = ws.alloc<unsigned long long>(nb);
       boff = ws.alloc<uint64_t>(uint64_t(nb) + 1);
       blk = ws.alloc<uint32_t>(uint64_t(G) * nb);

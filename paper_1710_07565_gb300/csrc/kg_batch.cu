@@ -67,6 +67,21 @@ struct BatchGeom {
     }
   }
   __device__ __forceinline__ uint64_t rows(uint64_t) const { return 0; }
+  // the sparse leaf kernel's map of a directed or rectangle tile (batch_desc
+  // routes only those, with aux0 = lo mod D and aux1 = the row of lo)
+  static __device__ __forceinline__ void sparse_tile_map(const TileDesc<BatchCtx>& td,
+                                                         SparseTileMap& m) {
+    const int kind = td.gx.kind;
+    m.D = kind == 0 ? td.gx.nm1 : td.gx.sj;
+    m.col0 = kind == 0 ? 0 : td.gx.rj;
+    m.skip = kind == 0;
+    m.y0 = td.aux0;
+    m.u0 = td.aux1;
+    if (!sparse_map_dev(m.D, m.M, m.s)) {
+      m.M = 0;
+      m.s = 0;
+    }
+  }
 };
 
 // Output positions below 2^62 go to the final output, those with bit 62 set
@@ -385,11 +400,15 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------- tile descriptors
+// Tiles of fewer draws stay with the general kernel, which packs several
+// tiles per CTA (the sparse kernel takes one tile per block).
+constexpr uint32_t BATCH_SPARSE_KMIN = 0;
+
 __global__ void __launch_bounds__(256)
     batch_desc(const BInst* __restrict__ inst, uint32_t count, uint64_t ntiles, uint32_t k_max,
                const uint64_t* __restrict__ tile_cnt, const uint64_t* __restrict__ tile_off,
                TileDesc<BatchCtx>* __restrict__ desc, unsigned long long* big,
-               unsigned long long* nbig, int* err) {
+               unsigned long long* nbig, int* err, bool sparse) {
   for (uint64_t t = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < ntiles;
        t += uint64_t(gridDim.x) * blockDim.x) {
     const uint32_t ii = find_inst(inst, count, t, 0);
@@ -418,6 +437,30 @@ __global__ void __launch_bounds__(256)
       x.sj = I.rb(uint64_t(j) + 1) - x.rj;
     }
     td.gx = x;
+    if (sparse && td.flags == 0) {
+      // the sparse leaf kernel takes directed and rectangle tiles whose map
+      // constants exist and whose in-row offsets stay below 2^(31+s); the
+      // general kernel samples the rest from the fallback list
+      bool ok = x.kind != 2 && td.k >= BATCH_SPARSE_KMIN && td.k <= uint32_t(SP_KMAX) &&
+                td.L > SP_NB;
+      if (ok) {
+        const uint64_t D = x.kind == 0 ? x.nm1 : x.sj;
+        uint32_t M;
+        int sh;
+        ok = sparse_map_dev(D, M, sh);
+        if (ok) {
+          const uint64_t q = x.kind == 0 ? div_q(x.div, td.lo) : rect_row(td.lo, D);
+          td.aux0 = td.lo - q * D;
+          td.aux1 = (x.kind == 0 ? x.r0 : x.ri) + q;
+          const uint64_t ymax = uint64_t(1) << (31 + sh);
+          ok = td.aux0 < ymax && td.L - 1 < ymax - td.aux0;
+        }
+      }
+      if (!ok) {
+        td.flags = 3;
+        big[ntiles - 1 - atomicAdd(nbig + 1, 1ull)] = t;
+      }
+    }
     if (td.flags == 1) big[atomicAdd(nbig, 1ull)] = t;
     desc[t] = td;
   }
@@ -644,7 +687,7 @@ static bool plan_carve(BatchPlan& bp, Workspace& ws) {
   bp.lvl_base = ws.alloc<uint64_t>(bp.level_nodes.size() * (count + 1));
   bp.desc = ws.alloc<TileDesc<BatchCtx>>(tiles);
   bp.big = ws.alloc<unsigned long long>(tiles);
-  bp.nbig = ws.alloc<unsigned long long>(1);
+  bp.nbig = ws.alloc<unsigned long long>(2);  // over k_max; left by the sparse kernel
   bp.pairs_buf = ws.alloc<uint32_t>(2 * pairs);
   bp.deg = ws.alloc<unsigned long long>(verts);
   bp.rowptr = ws.alloc<uint64_t>(verts + 1);
@@ -803,21 +846,33 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
   }
   int st = scan_exclusive_u64(bp->tile_cnt, bp->tile_off, bp->tiles, bp->scan_t, s);
   if (st) return st;
-  if (cudaMemsetAsync(bp->nbig, 0, 8, s) != cudaSuccess) return ST_CUDA;
+  if (cudaMemsetAsync(bp->nbig, 0, 16, s) != cudaSuccess) return ST_CUDA;
   {
     ProfScope ps(PROF_OTHER, s);
     batch_desc<<<grid_for(bp->tiles, 256, sm_count() * 32), 256, 0, s>>>(
         bp->inst, count, bp->tiles, K_MAX, bp->tile_cnt, bp->tile_off, bp->desc, bp->big,
-        bp->nbig, err);
+        bp->nbig, err, true);
     if (launch_ok()) return ST_CUDA;
   }
   BatchSink sink{out, bp->pairs_buf, cap, bp->pairs, err};
   const uint64_t gcap = bp->tiles < bp->leaf_grid_cap ? bp->tiles : bp->leaf_grid_cap;
-  {
+  if (bp->tiles) {
+    // directed and rectangle tiles without a repeated draw: the sparse kernel,
+    // one block per tile; the rest (triangles, dense tiles, repeated draws)
+    // from its fallback list by the general kernel
+    {
+      ProfScope ps(PROF_LEAF, s);
+      const unsigned grid = unsigned(bp->tiles < 0x7fffffffull ? bp->tiles : 0x7fffffffull);
+      leaf_sparse_kernel<BatchGeom, BatchSink, false, true><<<grid, SP_THREADS, 0, s>>>(
+          SparseMap{}, sink, RoundKeys{}, bp->desc, bp->tiles, err,
+          DigestOut{nullptr, nullptr, nullptr}, bp->big, bp->nbig + 1);
+      if (launch_ok()) return ST_CUDA;
+    }
     ProfScope ps(PROF_LEAF, s);
-    leaf_fast_kernel<BatchGeom, BatchSink, false, true><<<unsigned(gcap ? gcap : 1), FAST_THREADS, 0, s>>>(
+    const uint64_t lg = gcap < uint64_t(sm_count()) * 8 ? gcap : uint64_t(sm_count()) * 8;
+    leaf_fast_kernel<BatchGeom, BatchSink, false, true><<<unsigned(lg ? lg : 1), FAST_THREADS, 0, s>>>(
         BatchGeom{}, sink, 0, RoundKeys{}, bp->desc, bp->tiles, err,
-        DigestOut{nullptr, nullptr, nullptr});
+        DigestOut{nullptr, nullptr, nullptr}, bp->big, bp->nbig + 1);
     if (launch_ok()) return ST_CUDA;
   }
   {

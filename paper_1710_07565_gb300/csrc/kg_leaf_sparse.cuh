@@ -42,6 +42,26 @@ inline SparseMap sparse_map(uint64_t n) {
   return mp;
 }
 
+// The same constants for a row width D >= 4 on the device (s <= 30 keeps
+// 2^(32+s) in 64 bits); false if D is out of that range.
+__device__ __forceinline__ bool sparse_map_dev(uint64_t D, uint32_t& M, int& s) {
+  if (D < 4 || D >= (uint64_t(1) << 32)) return false;
+  s = 62 - __clzll(D);  // floor(log2 D) - 1
+  M = uint32_t((uint64_t(1) << (32 + s)) / D);
+  return true;
+}
+
+// Per-tile offset map of the sparse kernel for geometries whose row width
+// varies by tile: offset x of the tile is y = y0 + x past the start of row
+// u0; row u0 + floor(y / D), column position w = y mod D, and the column is
+// w + [w >= u] (directed: the diagonal is skipped) or col0 + w (a rectangle
+// of an undirected instance).
+struct SparseTileMap {
+  uint64_t D, y0, u0, col0;
+  uint32_t M;
+  int s, skip;
+};
+
 inline SparseRoute sparse_route(const SparseMap& mp, bool on) {
   SparseRoute r;
   r.on = on ? 1 : 0;
@@ -56,12 +76,17 @@ struct SparseSmem {
   uint32_t multi[SP_KMAX / 2];  // buckets holding several draws: start | count << 16
 };
 
-template <class Sink, bool DIGEST>
+// Geom: DirGeom (one map for the launch: mp, round keys rk), or a geometry
+// with a per-tile map (tile_map(td, map)) and per-tile seeds (TILE_SEED).
+template <class Geom, class Sink, bool DIGEST, bool TILE_SEED>
 __global__ void __launch_bounds__(SP_THREADS, SP_MIN_BLOCKS)
     leaf_sparse_kernel(SparseMap mp, Sink sink, RoundKeys rk,
-                       const TileDesc<DirGeom::Ctx>* __restrict__ desc, uint64_t ntiles, int* err,
-                       DigestOut dig, unsigned long long* __restrict__ list,
+                       const TileDesc<typename Geom::Ctx>* __restrict__ desc, uint64_t ntiles,
+                       int* err, DigestOut dig, unsigned long long* __restrict__ list,
                        unsigned long long* __restrict__ nlist) {
+  constexpr bool DIR = std::is_same<Geom, DirGeom>::value;
+  static_assert(DIR || !DIGEST, "the fused digest is for the directed geometry");
+  static_assert(DIR || TILE_SEED, "per-tile maps come with per-tile seeds");
   __shared__ __align__(16) SparseSmem sm;
   __shared__ unsigned bh[65];
   __shared__ __align__(16) uint32_t wsum[SP_THREADS / 32];
@@ -70,8 +95,9 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MIN_BLOCKS)
   __shared__ uint64_t s_fu, s_lu;
   __shared__ uint32_t s_fl, s_ll;
   __shared__ uint32_t s_nmulti;
-  using Desc = TileDesc<DirGeom::Ctx>;
+  using Desc = TileDesc<typename Geom::Ctx>;
   __shared__ __align__(16) Desc s_td[2];
+  __shared__ SparseTileMap s_map[2];  // per-tile maps (not DIR), staged with the descriptor
   const int tid = threadIdx.x;
   const int lane = tid & 31, wid = tid >> 5;
   auto stage = [&](uint64_t tt, int slot) {
@@ -79,6 +105,9 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MIN_BLOCKS)
     const uint32_t* src = reinterpret_cast<const uint32_t*>(desc + tt);
     uint32_t* dst = reinterpret_cast<uint32_t*>(&s_td[slot]);
     for (uint32_t w = tid; w < sizeof(Desc) / 4; w += SP_THREADS) dst[w] = src[w];
+    if constexpr (!DIR) {
+      if (tid == SP_THREADS - 1) Geom::sparse_tile_map(desc[tt], s_map[slot]);
+    }
   };
   uint4* const cnt4 = reinterpret_cast<uint4*>(sm.cnt);
 
@@ -112,7 +141,11 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MIN_BLOCKS)
       const uint32_t i = 2 * (tid + SP_THREADS * s);
       if (i < k) {
         uint32_t w[4];
-        philox10_rk(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, rk, w);
+        if constexpr (TILE_SEED)
+          philox10(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, uint32_t(td.seed),
+                   uint32_t(td.seed >> 32), w);
+        else
+          philox10_rk(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, rk, w);
         const uint64_t a = (uint64_t(w[0]) << 32) | w[1], c = (uint64_t(w[2]) << 32) | w[3];
         const uint64_t r0 = Lk + i + 1, r1 = r0 + 1;
         const uint64_t x0 = mul_hi64(a, r0), x1 = mul_hi64(c, r1);
@@ -233,7 +266,26 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MIN_BLOCKS)
     // ---- 4. emission: offset x of the tile is y = aux0 + x past the start of
     // row aux1; row u = aux1 + floor(y / D), column position w = y mod D,
     // v = w + [w >= u] (the diagonal is skipped)
-    const uint64_t rem0 = td.aux0, u0 = td.aux1, base = td.base;
+    const uint64_t base = td.base;
+    if constexpr (!DIR) {
+      const SparseTileMap& tm = s_map[cur];
+      const uint64_t rem0 = tm.y0, u0 = tm.u0, D = tm.D, col0 = tm.col0;
+      const uint32_t M = tm.M;
+      const int qs = tm.s, skip = tm.skip;
+      for (uint32_t r = tid; r < k; r += SP_THREADS) {
+        const uint64_t y = rem0 + sm.A[r];
+        uint32_t q = __umulhi(uint32_t(y >> qs), M);
+        uint64_t w = y - uint64_t(q) * D;
+        if (w >= D) {
+          w -= D;
+          ++q;
+        }
+        const uint64_t u = u0 + q;
+        sink.put(base + r, u, skip ? w + (w >= u ? 1 : 0) : col0 + w);
+      }
+      continue;
+    }
+    const uint64_t rem0 = td.aux0, u0 = td.aux1;
     const uint64_t D = mp.D;
     const uint32_t M = mp.M;
     const int qs = mp.s;

@@ -120,7 +120,7 @@ inline int launch_leaf(const Geom& g, const Sink& sink, uint64_t c_begin, int d,
       {
         ProfScope ps(PROF_LEAF, s);
         // one block per tile (a persistent grid of 1-16 waves measured no faster)
-        leaf_sparse_kernel<Sink, DIGEST><<<grid, SP_THREADS, 0, s>>>(
+        leaf_sparse_kernel<DirGeom, Sink, DIGEST, false><<<grid, SP_THREADS, 0, s>>>(
             mp, sink, round_keys(seed), desc, T, err, dig, big, nbig + 1);
         if (launch_ok()) return ST_CUDA;
       }

@@ -485,6 +485,10 @@ constexpr uint32_t ASM_NB_MAX = 16384;   // buckets (per-block histogram in shar
 constexpr uint32_t ASM_ROW_LANE = 8;     // rows up to this length are sorted by one thread
 constexpr uint32_t ASM_ROW_WARP = 256;   // ... up to this length by one warp, longer by the block
 
+constexpr int ASM_UNROLL = 4;          // pairs a thread loads before counting them
+constexpr int ASM_SCATTER_UNROLL = 4;  // ... before scattering them
+constexpr int ASM_HIST_BLOCKS = 2;     // count / scatter blocks per SM (64 KB histogram each)
+
 // contiguous share [i0, i1) of the np pairs for block `blk` of `nblk`
 __device__ __forceinline__ void asm_share(uint64_t np, uint32_t blk, uint32_t nblk, uint64_t& i0,
                                           uint64_t& i1) {
@@ -506,11 +510,18 @@ __global__ void __launch_bounds__(ASM_THREADS)
   __syncthreads();
   uint64_t i0, i1;
   asm_share(npairs_dev ? *npairs_dev : npairs_host, blockIdx.x, gridDim.x, i0, i1);
-  for (uint64_t i = i0 + threadIdx.x; i < i1; i += ASM_THREADS) {
-    uint64_t u, v;
-    load_pair(pairs, i, u, v);
-    if (u - row_lo < nrows) atomicAdd(&hcnt[(u - row_lo) >> bsh], 1u);
-    if (v - row_lo < nrows) atomicAdd(&hcnt[(v - row_lo) >> bsh], 1u);
+  for (uint64_t i = i0 + threadIdx.x; i < i1; i += ASM_UNROLL * ASM_THREADS) {
+    uint64_t u[ASM_UNROLL], v[ASM_UNROLL];
+#pragma unroll
+    for (int j = 0; j < ASM_UNROLL; ++j) {
+      u[j] = v[j] = ~uint64_t(0);  // outside every window
+      if (i + j * ASM_THREADS < i1) load_pair(pairs, i + j * ASM_THREADS, u[j], v[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < ASM_UNROLL; ++j) {
+      if (u[j] - row_lo < nrows) atomicAdd(&hcnt[(u[j] - row_lo) >> bsh], 1u);
+      if (v[j] - row_lo < nrows) atomicAdd(&hcnt[(v[j] - row_lo) >> bsh], 1u);
+    }
   }
   __syncthreads();
   uint32_t* row = blk + uint64_t(blockIdx.x) * nb;
@@ -555,24 +566,31 @@ __global__ void __launch_bounds__(ASM_THREADS)
   __syncthreads();
   uint64_t i0, i1;
   asm_share(npairs_dev ? *npairs_dev : npairs_host, blockIdx.x, gridDim.x, i0, i1);
-  for (uint64_t i = i0 + threadIdx.x; i < i1; i += ASM_THREADS) {
-    uint64_t u, v;
-    load_pair(pairs, i, u, v);
-    if (u - row_lo < nrows) {
-      const uint32_t b = uint32_t((u - row_lo) >> bsh);
-      const uint64_t p = boff[b] + atomicAdd(&hcur[b], 1u);
-      if (p < cap)
-        store_pair(out, p, u, v);
-      else
-        set_error(err, ST_CAPACITY);
+  for (uint64_t i = i0 + threadIdx.x; i < i1; i += ASM_SCATTER_UNROLL * ASM_THREADS) {
+    uint64_t u[ASM_SCATTER_UNROLL], v[ASM_SCATTER_UNROLL];
+#pragma unroll
+    for (int j = 0; j < ASM_SCATTER_UNROLL; ++j) {
+      u[j] = v[j] = ~uint64_t(0);  // outside every window
+      if (i + j * ASM_THREADS < i1) load_pair(pairs, i + j * ASM_THREADS, u[j], v[j]);
     }
-    if (v - row_lo < nrows) {
-      const uint32_t b = uint32_t((v - row_lo) >> bsh);
-      const uint64_t p = boff[b] + atomicAdd(&hcur[b], 1u);
-      if (p < cap)
-        store_pair(out, p, v, u);
-      else
-        set_error(err, ST_CAPACITY);
+#pragma unroll
+    for (int j = 0; j < ASM_SCATTER_UNROLL; ++j) {
+      if (u[j] - row_lo < nrows) {
+        const uint32_t b = uint32_t((u[j] - row_lo) >> bsh);
+        const uint64_t p = boff[b] + atomicAdd(&hcur[b], 1u);
+        if (p < cap)
+          store_pair(out, p, u[j], v[j]);
+        else
+          set_error(err, ST_CAPACITY);
+      }
+      if (v[j] - row_lo < nrows) {
+        const uint32_t b = uint32_t((v[j] - row_lo) >> bsh);
+        const uint64_t p = boff[b] + atomicAdd(&hcur[b], 1u);
+        if (p < cap)
+          store_pair(out, p, v[j], u[j]);
+        else
+          set_error(err, ST_CAPACITY);
+      }
     }
   }
 }
@@ -593,7 +611,9 @@ struct AsmSmem {
   uint64_t sorted[ASM_CAP];
   uint32_t rc[ASM_BR_MAX + 1];  // row counts -> row starts -> row cursors
   uint32_t nlong;
-  uint32_t longrow[ASM_BR_MAX];  // rows longer than ASM_ROW_SHORT
+  // rows longer than ASM_ROW_WARP: a bucket of at most ASM_CAP entries has
+  // fewer than ASM_CAP / ASM_ROW_WARP of them
+  uint32_t longrow[ASM_CAP / ASM_ROW_WARP];
 };
 
 // Sorts row[0, len), len <= 8, by one thread: the 8-input network of
