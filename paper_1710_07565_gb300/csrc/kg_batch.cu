@@ -67,22 +67,22 @@ struct BatchGeom {
     }
   }
   __device__ __forceinline__ uint64_t rows(uint64_t) const { return 0; }
-  // the sparse leaf kernel's map of a directed or rectangle tile (batch_desc
-  // routes only those, with aux0 = lo mod D and aux1 = the row of lo)
-  static __device__ __forceinline__ void sparse_tile_map(const TileDesc<BatchCtx>& td,
-                                                         SparseTileMap& m) {
-    const int kind = td.gx.kind;
-    m.D = kind == 0 ? td.gx.nm1 : td.gx.sj;
-    m.col0 = kind == 0 ? 0 : td.gx.rj;
-    m.skip = kind == 0;
-    m.y0 = td.aux0;
-    m.u0 = td.aux1;
-    if (!sparse_map_dev(m.D, m.M, m.s)) {
-      m.M = 0;
-      m.s = 0;
-    }
-  }
 };
+
+// The sparse leaf kernel's map of a directed or rectangle tile of a batch
+// (batch_desc routes only those, with aux0 = lo mod D and aux1 = the row of lo).
+__device__ __forceinline__ void sparse_tile_map(const TileDesc<BatchCtx>& td, SparseTileMap& m) {
+  const int kind = td.gx.kind;
+  m.D = kind == 0 ? td.gx.nm1 : td.gx.sj;
+  m.col0 = kind == 0 ? 0 : td.gx.rj;
+  m.skip = kind == 0;
+  m.y0 = td.aux0;
+  m.u0 = td.aux1;
+  if (!sparse_map_dev(m.D, m.M, m.s)) {
+    m.M = 0;
+    m.s = 0;
+  }
+}
 
 // Output positions below 2^62 go to the final output, those with bit 62 set
 // to the undirected pair scratch.

@@ -163,6 +163,42 @@ struct SparseRoute {
   uint64_t ymax;
 };
 
+// The same constants for a row width D >= 4 on the device (s <= 30 keeps
+// 2^(32+s) in 64 bits); false if D is out of that range.
+__device__ __forceinline__ bool sparse_map_dev(uint64_t D, uint32_t& M, int& s) {
+  if (D < 4 || D >= (uint64_t(1) << 32)) return false;
+  s = 62 - __clzll(D);  // floor(log2 D) - 1
+  M = uint32_t((uint64_t(1) << (32 + s)) / D);
+  return true;
+}
+
+// Per-tile offset map of the sparse kernel for geometries whose row width
+// varies by tile: offset x of the tile is y = y0 + x past the start of row
+// u0; row u0 + floor(y / D), column position w = y mod D, and the column is
+// w + [w >= u] (directed: the diagonal is skipped) or col0 + w (a rectangle
+// of an undirected instance).
+struct SparseTileMap {
+  uint64_t D, y0, u0, col0;
+  uint32_t M;
+  int s, skip;
+};
+
+// The map of a rectangle tile of an undirected geometry (the descriptor
+// kernel routes only those to the sparse kernel, with aux0 = lo mod s_j and
+// aux1 = the row of lo).
+__device__ __forceinline__ void sparse_tile_map(const TileDesc<UndGeom::Ctx>& td,
+                                                SparseTileMap& m) {
+  m.D = td.gx.sj;
+  m.col0 = td.gx.rj;
+  m.skip = 0;
+  m.y0 = td.aux0;
+  m.u0 = td.aux1;
+  if (!sparse_map_dev(m.D, m.M, m.s)) {
+    m.M = 0;
+    m.s = 0;
+  }
+}
+
 // Descriptors of tiles [0, ntiles) of chunks c_begin... .  Tiles over k_max go
 // to big[0 ..) (count nbig[0]), tiles routed away from the sparse kernel to
 // big[ntiles-1 ...) downwards (count nbig[1]); no tile is on both lists.
@@ -191,6 +227,28 @@ __global__ void __launch_bounds__(256)
       if (route.on && td.flags == 0) {
         const bool mapok = td.aux0 < route.ymax && td.L - 1 < route.ymax - td.aux0;
         if (td.k > uint32_t(SP_KMAX) || td.L <= SP_NB || !mapok) {
+          td.flags = 3;
+          big[ntiles - 1 - atomicAdd(nbig + 1, 1ull)] = t;
+        }
+      }
+    } else if constexpr (std::is_same<typename Geom::Ctx, UndGeom::Ctx>::value) {
+      // undirected: rectangle tiles with valid map constants go to the sparse
+      // kernel, triangles and the rest to its fallback list
+      if (route.on && td.flags == 0) {
+        bool ok = !td.gx.tri && td.k <= uint32_t(SP_KMAX) && td.L > SP_NB;
+        if (ok) {
+          uint32_t M;
+          int sh;
+          ok = sparse_map_dev(td.gx.sj, M, sh);
+          if (ok) {
+            const uint64_t q = rect_row(td.lo, td.gx.sj);
+            td.aux0 = td.lo - q * td.gx.sj;
+            td.aux1 = td.gx.ri + q;
+            const uint64_t ymax = uint64_t(1) << (31 + sh);
+            ok = td.aux0 < ymax && td.L - 1 < ymax - td.aux0;
+          }
+        }
+        if (!ok) {
           td.flags = 3;
           big[ntiles - 1 - atomicAdd(nbig + 1, 1ull)] = t;
         }

@@ -42,26 +42,6 @@ inline SparseMap sparse_map(uint64_t n) {
   return mp;
 }
 
-// The same constants for a row width D >= 4 on the device (s <= 30 keeps
-// 2^(32+s) in 64 bits); false if D is out of that range.
-__device__ __forceinline__ bool sparse_map_dev(uint64_t D, uint32_t& M, int& s) {
-  if (D < 4 || D >= (uint64_t(1) << 32)) return false;
-  s = 62 - __clzll(D);  // floor(log2 D) - 1
-  M = uint32_t((uint64_t(1) << (32 + s)) / D);
-  return true;
-}
-
-// Per-tile offset map of the sparse kernel for geometries whose row width
-// varies by tile: offset x of the tile is y = y0 + x past the start of row
-// u0; row u0 + floor(y / D), column position w = y mod D, and the column is
-// w + [w >= u] (directed: the diagonal is skipped) or col0 + w (a rectangle
-// of an undirected instance).
-struct SparseTileMap {
-  uint64_t D, y0, u0, col0;
-  uint32_t M;
-  int s, skip;
-};
-
 inline SparseRoute sparse_route(const SparseMap& mp, bool on) {
   SparseRoute r;
   r.on = on ? 1 : 0;
@@ -76,8 +56,9 @@ struct SparseSmem {
   uint32_t multi[SP_KMAX / 2];  // buckets holding several draws: start | count << 16
 };
 
-// Geom: DirGeom (one map for the launch: mp, round keys rk), or a geometry
-// with a per-tile map (tile_map(td, map)) and per-tile seeds (TILE_SEED).
+// Geom: DirGeom (one map for the launch: mp), or a geometry whose tiles carry
+// their own map (sparse_tile_map(descriptor, map)).  TILE_SEED: every tile
+// has its own seed (batched instances), else the round keys rk of the one seed.
 template <class Geom, class Sink, bool DIGEST, bool TILE_SEED>
 __global__ void __launch_bounds__(SP_THREADS, SP_MIN_BLOCKS)
     leaf_sparse_kernel(SparseMap mp, Sink sink, RoundKeys rk,
@@ -86,7 +67,6 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MIN_BLOCKS)
                        unsigned long long* __restrict__ nlist) {
   constexpr bool DIR = std::is_same<Geom, DirGeom>::value;
   static_assert(DIR || !DIGEST, "the fused digest is for the directed geometry");
-  static_assert(DIR || TILE_SEED, "per-tile maps come with per-tile seeds");
   __shared__ __align__(16) SparseSmem sm;
   __shared__ unsigned bh[65];
   __shared__ __align__(16) uint32_t wsum[SP_THREADS / 32];
@@ -106,7 +86,7 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MIN_BLOCKS)
     uint32_t* dst = reinterpret_cast<uint32_t*>(&s_td[slot]);
     for (uint32_t w = tid; w < sizeof(Desc) / 4; w += SP_THREADS) dst[w] = src[w];
     if constexpr (!DIR) {
-      if (tid == SP_THREADS - 1) Geom::sparse_tile_map(desc[tt], s_map[slot]);
+      if (tid == SP_THREADS - 1) sparse_tile_map(desc[tt], s_map[slot]);
     }
   };
   uint4* const cnt4 = reinterpret_cast<uint4*>(sm.cnt);

@@ -78,11 +78,25 @@ struct ChunkRunScratch {
 // replacements must be rare (tile width W >= 2^26 pairs: a 2048-draw tile
 // repeats a draw with probability below 1/32, a 1024-draw one below 1/128)
 // and n - 1 >= 4 for the map's quotient estimate.
+// The undirected geometry under a chunk-list geometry (or itself).
+inline const UndGeom& und_base(const UndGeom& g) { return g; }
+template <class G>
+inline const UndGeom& und_base(const G& g) {
+  return g.base;
+}
+
 template <class Geom>
 inline bool use_sparse_leaf(const Geom& g, uint64_t c_begin, int d) {
   if constexpr (std::is_same<Geom, DirGeom>::value) {
     if (g.n < 5) return false;
     return tile_width(g.universe(c_begin), d) >= (uint64_t(1) << 26);
+  } else if constexpr (std::is_same<typename Geom::Ctx, UndGeom::Ctx>::value) {
+    // undirected: the nominal rectangle chunk (row blocks of ceil(n / P) rows)
+    const UndGeom& b = und_base(g);
+    const u128 r = (u128(b.n) + b.P - 1) / b.P;
+    const u128 U = r * r;
+    if (r < 4 || (U >> 64)) return false;
+    return tile_width(uint64_t(U), d) >= (uint64_t(1) << 26);
   } else {
     return false;
   }
@@ -98,8 +112,10 @@ inline int launch_leaf(const Geom& g, const Sink& sink, uint64_t c_begin, int d,
   unsigned long long* nbig = sc.nbig;
   if (cudaMemsetAsync(nbig, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) return ST_CUDA;
   using Desc = TileDesc<typename Geom::Ctx>;
+  // undirected tiles without the fused digest also have a sparse path
+  constexpr bool SPARSE_UND = std::is_same<typename Geom::Ctx, UndGeom::Ctx>::value && !DIGEST;
   Desc* desc = sc.desc;
-  const bool sparse = use_sparse_leaf(g, c_begin, d);
+  const bool sparse = (std::is_same<Geom, DirGeom>::value || SPARSE_UND) && use_sparse_leaf(g, c_begin, d);
   SparseRoute route{0, 0};
   SparseMap mp{};
   if constexpr (std::is_same<Geom, DirGeom>::value) {
@@ -107,6 +123,8 @@ inline int launch_leaf(const Geom& g, const Sink& sink, uint64_t c_begin, int d,
       mp = sparse_map(g.n);
       route = sparse_route(mp, true);
     }
+  } else if constexpr (SPARSE_UND) {
+    route.on = sparse ? 1 : 0;  // per-tile maps: the descriptor kernel checks each tile
   }
   {
     ProfScope ps(PROF_OTHER, s);
@@ -115,12 +133,12 @@ inline int launch_leaf(const Geom& g, const Sink& sink, uint64_t c_begin, int d,
     if (launch_ok()) return ST_CUDA;
   }
   const unsigned grid = unsigned(T < 0x7fffffffull ? T : 0x7fffffffull);
-  if constexpr (std::is_same<Geom, DirGeom>::value) {
+  if constexpr (std::is_same<Geom, DirGeom>::value || SPARSE_UND) {
     if (sparse) {
       {
         ProfScope ps(PROF_LEAF, s);
         // one block per tile (a persistent grid of 1-16 waves measured no faster)
-        leaf_sparse_kernel<DirGeom, Sink, DIGEST, false><<<grid, SP_THREADS, 0, s>>>(
+        leaf_sparse_kernel<Geom, Sink, DIGEST, false><<<grid, SP_THREADS, 0, s>>>(
             mp, sink, round_keys(seed), desc, T, err, dig, big, nbig + 1);
         if (launch_ok()) return ST_CUDA;
       }
