@@ -740,12 +740,19 @@ __global__ void __launch_bounds__(ASM_THREADS)
     if (threadIdx.x < 65) sh_hist[threadIdx.x] = 0;
     if (threadIdx.x == 0) sh_dig = 0;
     __syncthreads();
-    for (uint32_t i = threadIdx.x; i < c; i += ASM_THREADS) {
-      uint64_t u, v;
-      load_pair(out, e0 + i, u, v);
-      const uint32_t rl = uint32_t(u - row_lo - r0);
-      sm.key[i] = (uint64_t(rl) << 48) | v;
-      atomicAdd(&sm.rc[rl], 1u);
+    // the bucket's entries, ASM_UNROLL loads in flight per thread
+    for (uint32_t i = threadIdx.x; i < c; i += ASM_UNROLL * ASM_THREADS) {
+      uint64_t u[ASM_UNROLL], v[ASM_UNROLL];
+#pragma unroll
+      for (int j = 0; j < ASM_UNROLL; ++j)
+        if (i + j * ASM_THREADS < c) load_pair(out, e0 + i + j * ASM_THREADS, u[j], v[j]);
+#pragma unroll
+      for (int j = 0; j < ASM_UNROLL; ++j)
+        if (i + j * ASM_THREADS < c) {
+          const uint32_t rl = uint32_t(u[j] - row_lo - r0);
+          sm.key[i + j * ASM_THREADS] = (uint64_t(rl) << 48) | v[j];
+          atomicAdd(&sm.rc[rl], 1u);
+        }
     }
     __syncthreads();
     // row starts: exclusive scan of the row counts (one thread per 8 rows)
