@@ -78,11 +78,39 @@ struct ChunkRunScratch {
 // replacements must be rare (tile width W >= 2^26 pairs: a 2048-draw tile
 // repeats a draw with probability below 1/32, a 1024-draw one below 1/128)
 // and n - 1 >= 4 for the map's quotient estimate.
+// Nominal universe of a run's chunks, on the host: the first chunk's
+// (directed), a rectangle of two row blocks of ceil(n / P) rows (undirected).
+template <class Geom>
+inline uint64_t nominal_universe(const Geom& g, uint64_t c_begin);
+
+// Tile-tree levels whose node universes are below EXACT_NODE_U draw exact
+// hypergeometrics (ratio of uniforms over five log-factorial terms, rejection
+// counts that differ from lane to lane): up to WARP_TREE_NODES_EXACT nodes
+// they also go one warp per node.  Larger universes take the binomial
+// approximation of the variate, cheap and even per lane, and go one lane per
+// node from WARP_TREE_NODES on.
+constexpr uint64_t WARP_TREE_NODES_EXACT = 16384;
+constexpr uint64_t EXACT_NODE_U = uint64_t(1) << 40;
+
 // The undirected geometry under a chunk-list geometry (or itself).
 inline const UndGeom& und_base(const UndGeom& g) { return g; }
 template <class G>
 inline const UndGeom& und_base(const G& g) {
   return g.base;
+}
+
+template <class Geom>
+inline uint64_t nominal_universe(const Geom& g, uint64_t c_begin) {
+  if constexpr (std::is_same<Geom, DirGeom>::value) {
+    return g.universe(c_begin);
+  } else if constexpr (std::is_same<typename Geom::Ctx, UndGeom::Ctx>::value) {
+    const UndGeom& b = und_base(g);
+    const u128 r = (u128(b.n) + b.P - 1) / b.P;
+    const u128 U = r * r;
+    return (U >> 64) ? ~uint64_t(0) : uint64_t(U);
+  } else {
+    return ~uint64_t(0);
+  }
 }
 
 template <class Geom>
@@ -178,7 +206,8 @@ int run_chunks_carved(const Geom& g, uint64_t c_begin, uint64_t C, const uint64_
     uint64_t* out = (level & 1) ? sc.B : sc.A;
     const uint64_t nodes = C << level;
     ProfScope ps(PROF_TILE_TREE, s);
-    if (nodes <= WARP_TREE_NODES)
+    if (nodes <= WARP_TREE_NODES ||
+        (nodes <= WARP_TREE_NODES_EXACT && (nominal_universe(g, c_begin) >> level) < EXACT_NODE_U))
       // few nodes: one warp per variate, so that the level waits for one
       // variate's chain instead of the slowest of 32 lanes
       tile_tree_level_warp<Geom><<<grid_for(nodes, 4, sm_count() * 64), 128, 0, s>>>(
