@@ -47,6 +47,9 @@ static int check_undirected(uint64_t n, uint64_t m, uint32_t P, uint32_t k_leaf,
   return ST_OK;
 }
 
+// Levels with at least this many nodes (bound) take the 64-register quad_level.
+constexpr uint64_t QUAD_WIDE_NODES = uint64_t(1) << 18;
+
 // Quadrant recursion: levels 0..D, node lists ping-pong, leaf counts per chunk.
 static int run_quadtree(const UndParams& up, uint64_t seed, uint64_t* chunk_cnt, Workspace& ws,
                         cudaStream_t s, int* err) {
@@ -65,8 +68,13 @@ static int run_quadtree(const UndParams& up, uint64_t seed, uint64_t* chunk_cnt,
     const uint64_t bound = (l < 16) ? ((uint64_t(1) << l) * ((uint64_t(1) << l) + 1) / 2) : C;
     ProfScope ps(PROF_CHUNK_TREE, s);
     // one-warp blocks spread the few FP64-bound nodes of the top levels over the SMs
-    quad_level<<<grid_for(bound < C ? bound : C, 32, sm_count() * 64), 32, 0, s>>>(
-        rb, seed, (l & 1) ? L1 : L0, counts + l, (l & 1) ? L0 : L1, counts + l + 1, chunk_cnt, err);
+    const uint64_t nodes = bound < C ? bound : C;
+    if (nodes >= QUAD_WIDE_NODES)
+      quad_level<4><<<grid_for(nodes, 32, sm_count() * 64), 32, 0, s>>>(
+          rb, seed, (l & 1) ? L1 : L0, counts + l, (l & 1) ? L0 : L1, counts + l + 1, chunk_cnt, err);
+    else
+      quad_level<1><<<grid_for(nodes, 32, sm_count() * 64), 32, 0, s>>>(
+          rb, seed, (l & 1) ? L1 : L0, counts + l, (l & 1) ? L0 : L1, counts + l + 1, chunk_cnt, err);
     if (launch_ok()) return ST_CUDA;
   }
   return ST_OK;

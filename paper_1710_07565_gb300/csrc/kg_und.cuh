@@ -39,9 +39,11 @@ static __global__ void quad_init(QNode* list, uint32_t* counts, int nlevels, uin
 //    X2 = Hyp(N - |T1|, |R|, cnt - X1), T2 gets the rest;
 //  - rectangle: each dimension with more than one block halved at ceil, the
 //    parts in row-major order, sequential conditional hypergeometrics.
-// (64 registers: the spills cost less than the occupancy they buy, measured
-// 62 -> 47 ms for the 8.4 M-chunk tree at P = 4096)
-static __global__ void __launch_bounds__(256, 4)
+// MINB = 4 (64 registers) for wide levels, where the spills cost less than
+// the occupancy they buy (62 -> 47 ms for the 8.4 M-chunk tree at P = 4096);
+// narrow levels are latency-bound and keep all the registers they want.
+template <int MINB>
+static __global__ void __launch_bounds__(256, MINB)
     quad_level(RowBounds rb, uint64_t seed, const QNode* __restrict__ in,
                const uint32_t* __restrict__ nin, QNode* __restrict__ out, uint32_t* nout,
                uint64_t* __restrict__ chunk_cnt, int* err) {
