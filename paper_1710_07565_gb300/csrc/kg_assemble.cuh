@@ -49,6 +49,8 @@ struct AsmScratch {
   // bucketed path
   unsigned long long *bcnt = nullptr, *big = nullptr, *nbig = nullptr;
   uint32_t* blk = nullptr;  // G rows of nb per-block bucket counts, then offsets
+  uint64_t* keys = nullptr;  // the scattered entries as 8-byte keys (asm_key), kcap of them
+  uint64_t kcap = 0;
   uint32_t G = 0;           // blocks of the count and scatter kernels
   uint64_t* boff = nullptr;
   // atomic path
@@ -64,6 +66,8 @@ struct AsmScratch {
       bcnt = ws.alloc<unsigned long long>(nb);
       boff = ws.alloc<uint64_t>(uint64_t(nb) + 1);
       blk = ws.alloc<uint32_t>(uint64_t(G) * nb);
+      kcap = expect;
+      keys = ws.alloc<uint64_t>(kcap ? kcap : 1);
       big = ws.alloc<unsigned long long>(nb);
       nbig = ws.alloc<unsigned long long>(1);
       if (!scan_scratch(nb, ws, scan)) return false;
@@ -127,20 +131,20 @@ inline int assemble_buckets(const Id* pairs, const uint64_t* npairs_dev, uint64_
   {
     ProfScope ps(PROF_ASSEMBLY, s);
     asm_bucket_scatter<Id><<<G, ASM_THREADS, hsm, s>>>(pairs, npairs_dev, npairs_host, row_lo,
-                                                       nrows, bsh, nb, sc.boff, sc.blk, out, cap,
-                                                       err);
+                                                       nrows, bsh, nb, sc.boff, sc.blk, sc.keys,
+                                                       sc.kcap, err);
     if (launch_ok()) return ST_CUDA;
   }
   {
     ProfScope ps(PROF_ASSEMBLY, s);
     asm_bucket_sort<Id><<<grid_for(nb, 1, sm_count() * 4), ASM_THREADS, sizeof(AsmSmem), s>>>(
-        out, sc.boff, row_lo, nrows, bsh, nb, cap, sc.rowptr, sc.big, sc.nbig, dig);
+        out, sc.keys, sc.boff, row_lo, nrows, bsh, nb, cap, sc.rowptr, sc.big, sc.nbig, dig);
     if (launch_ok()) return ST_CUDA;
   }
   {
     ProfScope ps(PROF_ASSEMBLY, s);
-    asm_bucket_sort_global<Id><<<sm_count(), ASM_THREADS, 0, s>>>(out, sc.boff, row_lo, nrows, bsh,
-                                                                   sc.rowptr, sc.big, sc.nbig, dig);
+    asm_bucket_sort_global<Id><<<sm_count(), ASM_THREADS, 0, s>>>(
+        out, sc.keys, sc.boff, row_lo, nrows, bsh, sc.rowptr, sc.big, sc.nbig, dig);
     if (launch_ok()) return ST_CUDA;
   }
   // the window's last offset: its entry count

@@ -489,6 +489,14 @@ constexpr uint32_t ASM_NB_MAX = 16384;   // buckets (per-block histogram in shar
 constexpr uint32_t ASM_ROW_LANE = 8;     // rows up to this length are sorted by one thread
 constexpr uint32_t ASM_ROW_WARP = 256;   // ... up to this length by one warp, longer by the block
 
+// An entry of a bucket as 8 bytes: its row inside the bucket (< 2^16) above
+// bit 48, its column (< 2^48) below.  The scatter writes these keys to a
+// staging array (half the bytes of a uint64 pair) and the bucket sort turns
+// them back into (row, column) entries.
+__device__ __forceinline__ uint64_t asm_key(uint64_t row_in_bucket, uint64_t col) {
+  return (row_in_bucket << 48) | col;
+}
+
 constexpr int ASM_UNROLL = 4;          // pairs a thread loads before counting them
 constexpr int ASM_SCATTER_UNROLL = 4;  // ... before scattering them
 constexpr int ASM_HIST_BLOCKS = 2;     // count / scatter blocks per SM (64 KB histogram each)
@@ -563,7 +571,7 @@ __global__ void __launch_bounds__(ASM_THREADS)
     asm_bucket_scatter(const Id* __restrict__ pairs, const uint64_t* __restrict__ npairs_dev,
                        uint64_t npairs_host, uint64_t row_lo, uint64_t nrows, int bsh, uint32_t nb,
                        const uint64_t* __restrict__ boff, const uint32_t* __restrict__ blk,
-                       Id* __restrict__ out, uint64_t cap, int* err) {
+                       uint64_t* __restrict__ keys, uint64_t kcap, int* err) {
   extern __shared__ uint32_t hcur[];  // per bucket: this block's next slot in it
   const uint32_t* row = blk + uint64_t(blockIdx.x) * nb;
   for (uint32_t i = threadIdx.x; i < nb; i += ASM_THREADS) hcur[i] = row[i];
@@ -580,18 +588,20 @@ __global__ void __launch_bounds__(ASM_THREADS)
 #pragma unroll
     for (int j = 0; j < ASM_SCATTER_UNROLL; ++j) {
       if (u[j] - row_lo < nrows) {
-        const uint32_t b = uint32_t((u[j] - row_lo) >> bsh);
+        const uint64_t rl = u[j] - row_lo;
+        const uint32_t b = uint32_t(rl >> bsh);
         const uint64_t p = boff[b] + atomicAdd(&hcur[b], 1u);
-        if (p < cap)
-          store_pair(out, p, u[j], v[j]);
+        if (p < kcap)
+          keys[p] = asm_key(rl & ((uint64_t(1) << bsh) - 1), v[j]);
         else
           set_error(err, ST_CAPACITY);
       }
       if (v[j] - row_lo < nrows) {
-        const uint32_t b = uint32_t((v[j] - row_lo) >> bsh);
+        const uint64_t rl = v[j] - row_lo;
+        const uint32_t b = uint32_t(rl >> bsh);
         const uint64_t p = boff[b] + atomicAdd(&hcur[b], 1u);
-        if (p < cap)
-          store_pair(out, p, v[j], u[j]);
+        if (p < kcap)
+          keys[p] = asm_key(rl & ((uint64_t(1) << bsh) - 1), u[j]);
         else
           set_error(err, ST_CAPACITY);
       }
@@ -713,7 +723,8 @@ __device__ __forceinline__ void asm_block_sort(uint64_t* x, uint32_t n) {
 // Buckets over ASM_CAP entries go to big (sorted by asm_bucket_sort_global).
 template <class Id>
 __global__ void __launch_bounds__(ASM_THREADS)
-    asm_bucket_sort(Id* __restrict__ out, const uint64_t* __restrict__ boff, uint64_t row_lo,
+    asm_bucket_sort(Id* __restrict__ out, const uint64_t* __restrict__ keys,
+                    const uint64_t* __restrict__ boff, uint64_t row_lo,
                     uint64_t nrows, int bsh, uint32_t nb, uint64_t cap,
                     uint64_t* __restrict__ rowptr, unsigned long long* __restrict__ big,
                     unsigned long long* __restrict__ nbig, AsmDigest dig) {
@@ -742,18 +753,17 @@ __global__ void __launch_bounds__(ASM_THREADS)
     if (threadIdx.x < 65) sh_hist[threadIdx.x] = 0;
     if (threadIdx.x == 0) sh_dig = 0;
     __syncthreads();
-    // the bucket's entries, ASM_UNROLL loads in flight per thread
+    // the bucket's keys, ASM_UNROLL loads in flight per thread
     for (uint32_t i = threadIdx.x; i < c; i += ASM_UNROLL * ASM_THREADS) {
-      uint64_t u[ASM_UNROLL], v[ASM_UNROLL];
+      uint64_t k[ASM_UNROLL];
 #pragma unroll
       for (int j = 0; j < ASM_UNROLL; ++j)
-        if (i + j * ASM_THREADS < c) load_pair(out, e0 + i + j * ASM_THREADS, u[j], v[j]);
+        if (i + j * ASM_THREADS < c) k[j] = keys[e0 + i + j * ASM_THREADS];
 #pragma unroll
       for (int j = 0; j < ASM_UNROLL; ++j)
         if (i + j * ASM_THREADS < c) {
-          const uint32_t rl = uint32_t(u[j] - row_lo - r0);
-          sm.key[i + j * ASM_THREADS] = (uint64_t(rl) << 48) | v[j];
-          atomicAdd(&sm.rc[rl], 1u);
+          sm.key[i + j * ASM_THREADS] = k[j];
+          atomicAdd(&sm.rc[uint32_t(k[j] >> 48)], 1u);
         }
     }
     __syncthreads();
@@ -873,9 +883,9 @@ __global__ void __launch_bounds__(ASM_THREADS)
 // by binary search.
 template <class Id>
 __global__ void __launch_bounds__(ASM_THREADS)
-    asm_bucket_sort_global(Id* __restrict__ out, const uint64_t* __restrict__ boff,
-                           uint64_t row_lo, uint64_t nrows, int bsh,
-                           uint64_t* __restrict__ rowptr,
+    asm_bucket_sort_global(Id* __restrict__ out, uint64_t* __restrict__ keys,
+                           const uint64_t* __restrict__ boff, uint64_t row_lo, uint64_t nrows,
+                           int bsh, uint64_t* __restrict__ rowptr,
                            const unsigned long long* __restrict__ big,
                            const unsigned long long* __restrict__ nbig, AsmDigest dig) {
   const unsigned long long nb = *nbig;
@@ -884,29 +894,23 @@ __global__ void __launch_bounds__(ASM_THREADS)
     const uint64_t e0 = boff[b], n = boff[b + 1] - e0;
     const uint64_t r0 = uint64_t(b) << bsh;
     const uint64_t nr = nrows - r0 < (uint64_t(1) << bsh) ? nrows - r0 : (uint64_t(1) << bsh);
-    auto get = [&](uint64_t i, uint64_t& u, uint64_t& v) { load_pair(out, e0 + i, u, v); };
-    auto less = [](uint64_t u1, uint64_t v1, uint64_t u2, uint64_t v2) {
-      return u1 < u2 || (u1 == u2 && v1 < v2);
-    };
+    uint64_t* x = keys + e0;
     uint64_t N = 1;
     int lgN = 0;
     while (N < n) {
       N <<= 1;
       ++lgN;
     }
+    // bitonic sort of the bucket's keys in place (positions past n act as +infinity)
     for (int lk = 1; lk <= lgN; ++lk) {
       const uint64_t k = uint64_t(1) << lk;
       for (uint64_t i = threadIdx.x; i < N / 2; i += ASM_THREADS) {
         const uint64_t blk = i >> (lk - 1), off = i & (k / 2 - 1);
         const uint64_t lo = blk * k + off, hi = blk * k + k - 1 - off;
-        if (hi < n) {
-          uint64_t ul, vl, uh, vh;
-          get(lo, ul, vl);
-          get(hi, uh, vh);
-          if (less(uh, vh, ul, vl)) {
-            store_pair(out, e0 + lo, uh, vh);
-            store_pair(out, e0 + hi, ul, vl);
-          }
+        if (hi < n && x[hi] < x[lo]) {
+          const uint64_t t = x[lo];
+          x[lo] = x[hi];
+          x[hi] = t;
         }
       }
       __syncthreads();
@@ -915,28 +919,23 @@ __global__ void __launch_bounds__(ASM_THREADS)
         for (uint64_t i = threadIdx.x; i < N / 2; i += ASM_THREADS) {
           const uint64_t blk = i >> lj, off = i & (j - 1);
           const uint64_t lo = blk * 2 * j + off, hi = lo + j;
-          if (hi < n) {
-            uint64_t ul, vl, uh, vh;
-            get(lo, ul, vl);
-            get(hi, uh, vh);
-            if (less(uh, vh, ul, vl)) {
-              store_pair(out, e0 + lo, uh, vh);
-              store_pair(out, e0 + hi, ul, vl);
-            }
+          if (hi < n && x[hi] < x[lo]) {
+            const uint64_t t = x[lo];
+            x[lo] = x[hi];
+            x[hi] = t;
           }
         }
         __syncthreads();
       }
     }
-    // first entry of every row of the bucket
+    // the entries in order, and the first entry of every row of the bucket
+    for (uint64_t i = threadIdx.x; i < n; i += ASM_THREADS)
+      store_pair(out, e0 + i, row_lo + r0 + (x[i] >> 48), x[i] & ((uint64_t(1) << 48) - 1));
     for (uint64_t r = threadIdx.x; r < nr; r += ASM_THREADS) {
-      const uint64_t row = row_lo + r0 + r;
       uint64_t a = 0, e = n;
       while (a < e) {
         const uint64_t mid = (a + e) >> 1;
-        uint64_t u, v;
-        get(mid, u, v);
-        if (u < row)
+        if ((x[mid] >> 48) < r)
           a = mid + 1;
         else
           e = mid;
@@ -951,11 +950,7 @@ __global__ void __launch_bounds__(ASM_THREADS)
         const uint64_t row = row_lo + r0 + r;
         const uint64_t bi = block_of_row(dig.rb, row) - dig.b_lo;
         unsigned long long ds = 0;
-        for (uint64_t e = s0; e < s1; ++e) {
-          uint64_t u, v;
-          load_pair(out, e, u, v);
-          ds += edge_hash(u, v);
-        }
+        for (uint64_t e = s0; e < s1; ++e) ds += edge_hash(row, keys[e] & ((uint64_t(1) << 48) - 1));
         if (dig.digest && ds) atomicAdd(&dig.digest[bi], ds);
         if (dig.hist) atomicAdd(&dig.hist[bi * 65 + (s1 - s0 < 64 ? s1 - s0 : 64)], 1ull);
       }
