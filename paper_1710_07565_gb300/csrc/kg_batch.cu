@@ -658,7 +658,7 @@ struct BatchPlan {
   // the big instances run on big_lanes streams forked from the caller's
   // stream and joined back (capturable): big k on lane big_lane[k], chosen
   // largest first onto the least loaded lane; one lane is the caller's stream
-  static constexpr int BIG_LANES = 4;
+  static constexpr int BIG_LANES = 8;
   int big_lanes = 1;
   std::vector<int> big_lane;
   cudaStream_t big_s[BIG_LANES] = {};

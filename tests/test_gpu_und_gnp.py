@@ -26,6 +26,10 @@ UND_CASES = [
     (3000, 40000, 11, 1, 8, 64, 100),        # one triangle chunk
     (777, 5000, 13, 777, 4, 3, 5),           # one vertex per block
     (2, 1, 15, 2, 4, 1024, 2048),
+    # rectangle tiles of 2^26 pairs (576 tiles of ~1000 draws): the sparse leaf
+    # kernel, about one tile in 128 with a repeated draw (its fallback list)
+    (1 << 18, 512000, 17, 8, 4, 1024, 2048),
+    (1 << 18, 512000, 18, 8, 8, 1024, 2048),
 ]
 
 
