@@ -241,10 +241,16 @@ kg_status kg_gnm_directed_noalloc_scratch(uint64_t n, uint64_t m, uint32_t chunk
  * [offsets[i], offsets[i+1]) of d_out (kg_batch_offsets) and is bit-identical
  * to what kg_gnm_directed / kg_gnm_undirected write for the same instance
  * (uint32 ids only: id_bytes must be 4).  Limits per instance: chunks <= 64
- * (directed) or <= 32 (undirected), n <= 2^32, m <= 2^44.
+ * (directed) or <= 32 (undirected), n <= 2^32, m <= 2^44.  Undirected
+ * instances of 2^20 pairs or more are assembled on up to 8 stream lanes: the
+ * caller's stream and up to 7 streams that kg_batch_create creates (forked
+ * from `stream` by events and joined back, so that all of kg_batch_run's
+ * work is ordered before what follows on `stream`); kg_batch_destroy
+ * releases them.  One batch runs on one stream at a time.
  * kg_batch_tune times the launch shapes that do not change the output
- * (threads per block of the tree kernel: 64, 128, 256; tiles per CTA of the
- * leaf kernel: 1, 2, 4, 8, 16) on the caller's buffer and keeps the fastest.
+ * (threads per block of the chunk-count kernel: 64, 128, 256; tiles per CTA
+ * of the general leaf kernel, which samples the tiles the sparse leaf kernel
+ * leaves: 1, 2, 4, 8, 16) on the caller's buffer and keeps the fastest.
  * Choices are cached for the process by GPU name and size class (log2 of the
  * instance and tile counts): a batch of a class already tuned on the same GPU
  * takes the cached choice without timing.  kg_batch_get_tuning reports the
