@@ -794,7 +794,9 @@ int batch_layout(const BatchSpec* specs, uint32_t count, std::vector<BInst>& tab
     for (size_t k = 0; k < order.size(); ++k) order[k] = k;
     std::stable_sort(order.begin(), order.end(),
                      [&](size_t a, size_t b) { return bp.bigs[a].m > bp.bigs[b].m; });
+    // lane 0 (the caller's stream) also assembles the small instances first
     std::vector<uint64_t> load(size_t(bp.big_lanes), 0);
+    load[0] = spairs;
     for (size_t k : order) {
       const int l = int(std::min_element(load.begin(), load.end()) - load.begin());
       bp.big_lane[k] = l;
@@ -863,8 +865,8 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
     {
       ProfScope ps(PROF_LEAF, s);
       const unsigned grid = unsigned(bp->tiles < 0x7fffffffull ? bp->tiles : 0x7fffffffull);
-      leaf_sparse_kernel<BatchGeom, BatchSink, false, true><<<grid, SP_THREADS, 0, s>>>(
-          SparseMap{}, sink, RoundKeys{}, bp->desc, bp->tiles, err,
+      leaf_sparse_kernel<BatchGeom, BatchSink, false><<<grid, SP_THREADS, 0, s>>>(
+          SparseMap{}, sink, bp->desc, bp->tiles, err,
           DigestOut{nullptr, nullptr, nullptr}, bp->big, bp->nbig + 1);
       if (launch_ok()) return ST_CUDA;
     }
@@ -882,14 +884,11 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
         bp->nbig);
     if (launch_ok()) return ST_CUDA;
   }
-  if (bp->has_und) {
-    st = batch_assemble_small(bp, out, cap, s, err);
-    if (st) return st;
-  }
-  if (bp->bigs.empty()) return ST_OK;
+  if (bp->bigs.empty()) return bp->has_und ? batch_assemble_small(bp, out, cap, s, err) : ST_OK;
   // the big undirected instances, each by the per-instance assembly, on
-  // big_lanes streams (lane 0 is s); a lane's scratch area is reused in its
-  // stream order
+  // big_lanes streams (lane 0 is s, which first assembles the small
+  // instances, concurrently with the other lanes' big ones); a lane's scratch
+  // area is reused in its stream order
   const int nl = bp->big_lanes;
   cudaStream_t lane_s[BatchPlan::BIG_LANES];
   lane_s[0] = s;
@@ -901,6 +900,7 @@ static int batch_run_impl(BatchPlan* bp, uint32_t* out, uint64_t cap, cudaStream
       if (cudaStreamWaitEvent(lane_s[l], bp->big_ev[0], 0) != cudaSuccess) return ST_CUDA;
     forked = true;
   }
+  if (bp->has_und) st = batch_assemble_small(bp, out, cap, s, err);
   for (size_t k = 0; k < bp->bigs.size() && st == ST_OK; ++k) {
     const auto& g = bp->bigs[k];
     const int l = bp->big_lane[k];

@@ -57,11 +57,12 @@ struct SparseSmem {
 };
 
 // Geom: DirGeom (one map for the launch: mp), or a geometry whose tiles carry
-// their own map (sparse_tile_map(descriptor, map)).  TILE_SEED: every tile
-// has its own seed (batched instances), else the round keys rk of the one seed.
-template <class Geom, class Sink, bool DIGEST, bool TILE_SEED>
+// their own map (sparse_tile_map(descriptor, map)).  The Philox keys come from
+// each tile's seed, added up round by round: holding ten precomputed round
+// keys in registers measured slower here (more spills at 5 blocks per SM).
+template <class Geom, class Sink, bool DIGEST>
 __global__ void __launch_bounds__(SP_THREADS, SP_MIN_BLOCKS)
-    leaf_sparse_kernel(SparseMap mp, Sink sink, RoundKeys rk,
+    leaf_sparse_kernel(SparseMap mp, Sink sink,
                        const TileDesc<typename Geom::Ctx>* __restrict__ desc, uint64_t ntiles,
                        int* err, DigestOut dig, unsigned long long* __restrict__ list,
                        unsigned long long* __restrict__ nlist) {
@@ -121,11 +122,8 @@ __global__ void __launch_bounds__(SP_THREADS, SP_MIN_BLOCKS)
       const uint32_t i = 2 * (tid + SP_THREADS * s);
       if (i < k) {
         uint32_t w[4];
-        if constexpr (TILE_SEED)
-          philox10(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, uint32_t(td.seed),
-                   uint32_t(td.seed >> 32), w);
-        else
-          philox10_rk(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, rk, w);
+        philox10(i >> 1, uint32_t(node), uint32_t(node >> 32), TAG_LEAF, uint32_t(td.seed),
+                 uint32_t(td.seed >> 32), w);
         const uint64_t a = (uint64_t(w[0]) << 32) | w[1], c = (uint64_t(w[2]) << 32) | w[3];
         const uint64_t r0 = Lk + i + 1, r1 = r0 + 1;
         const uint64_t x0 = mul_hi64(a, r0), x1 = mul_hi64(c, r1);

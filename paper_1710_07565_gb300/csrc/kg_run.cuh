@@ -166,8 +166,8 @@ inline int launch_leaf(const Geom& g, const Sink& sink, uint64_t c_begin, int d,
       {
         ProfScope ps(PROF_LEAF, s);
         // one block per tile (a persistent grid of 1-16 waves measured no faster)
-        leaf_sparse_kernel<Geom, Sink, DIGEST, false><<<grid, SP_THREADS, 0, s>>>(
-            mp, sink, round_keys(seed), desc, T, err, dig, big, nbig + 1);
+        leaf_sparse_kernel<Geom, Sink, DIGEST><<<grid, SP_THREADS, 0, s>>>(
+            mp, sink, desc, T, err, dig, big, nbig + 1);
         if (launch_ok()) return ST_CUDA;
       }
       // the tiles the sparse kernel left (usually none): a fixed grid that
