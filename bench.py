@@ -32,8 +32,8 @@ SLAB_CAP = (1 << 29) + (1 << 21)  # edges per slab buffer (mean 2^29, sd ~2^14.5
 # DRAM bytes (read + write) per edge of the leaf kernel (leaf_sparse_kernel),
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of its
 # launch on chunks [0, 256) of this workload (python bench.py --profile-chunks
-# 256): 494,273,792 B / 33,550,402 edges; scaled to a slab launch by its edges.
-LEAF_TRAFFIC_PER_EDGE = (488850432 + 5423360) / 33550402
+# 256): 491,073,792 B / 33,550,402 edges; scaled to a slab launch by its edges.
+LEAF_TRAFFIC_PER_EDGE = (485669376 + 5404416) / 33550402
 ID_BYTES = 8
 WORKLOAD = "directed G(n,m): n=2^36, m=2^33, 2^16 chunks, uint64 ids, 16 slabs of 8 GiB, per-chunk digest + out-degree histogram"
 METRIC = "edges/s (directed G(n,m), n=2^36, m=2^33, 2^16 chunks, uint64 ids, on-device digest)"
