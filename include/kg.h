@@ -242,7 +242,7 @@ kg_status kg_gnm_directed_noalloc_scratch(uint64_t n, uint64_t m, uint32_t chunk
  * to what kg_gnm_directed / kg_gnm_undirected write for the same instance
  * (uint32 ids only: id_bytes must be 4).  Limits per instance: chunks <= 64
  * (directed) or <= 32 (undirected), n <= 2^32, m <= 2^44.  Undirected
- * instances of 2^20 pairs or more are assembled on up to 8 stream lanes: the
+ * instances of 2^19 pairs or more are assembled on up to 8 stream lanes: the
  * caller's stream and up to 7 streams that kg_batch_create creates (forked
  * from `stream` by events and joined back, so that all of kg_batch_run's
  * work is ordered before what follows on `stream`); kg_batch_destroy

@@ -670,7 +670,7 @@ struct BatchPlan {
   void* mem = nullptr;  // the plan's device memory (kg_batch_create), one allocation
 };
 
-constexpr uint64_t BIG_PAIRS = uint64_t(1) << 20;
+constexpr uint64_t BIG_PAIRS = uint64_t(1) << 19;
 
 static uint64_t piece(uint64_t b) { return (b + 255) & ~uint64_t(255); }
 
