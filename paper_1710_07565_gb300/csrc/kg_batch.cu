@@ -400,9 +400,6 @@ __global__ void __launch_bounds__(256)
 }
 
 // ---------------------------------------------------------------- tile descriptors
-// Tiles of fewer draws stay with the general kernel, which packs several
-// tiles per CTA (the sparse kernel takes one tile per block).
-constexpr uint32_t BATCH_SPARSE_KMIN = 0;
 
 __global__ void __launch_bounds__(256)
     batch_desc(const BInst* __restrict__ inst, uint32_t count, uint64_t ntiles, uint32_t k_max,
@@ -441,8 +438,7 @@ __global__ void __launch_bounds__(256)
       // the sparse leaf kernel takes directed and rectangle tiles whose map
       // constants exist and whose in-row offsets stay below 2^(31+s); the
       // general kernel samples the rest from the fallback list
-      bool ok = x.kind != 2 && td.k >= BATCH_SPARSE_KMIN && td.k <= uint32_t(SP_KMAX) &&
-                td.L > SP_NB;
+      bool ok = x.kind != 2 && td.k <= uint32_t(SP_KMAX) && td.L > SP_NB;
       if (ok) {
         const uint64_t D = x.kind == 0 ? x.nm1 : x.sj;
         uint32_t M;
