@@ -661,6 +661,21 @@ def profile_und_rows(kg, ranges):
     print(json.dumps({"profile_und_rows": ranges, "entries": int(ent.sum())}))
 
 
+def profile_config1(kg, calls):
+    """Directed G(n,m) at n = 2^16, m = 2^20, 64 chunks, uint32 ids (the
+    per-instance latency case), `calls` calls on one stream (the case of its
+    launch list under profiles/)."""
+    import torch
+    s = torch.cuda.current_stream().cuda_stream
+    n, m, P = 1 << 16, 1 << 20, 64
+    out = torch.empty((m, 2), dtype=torch.int32, device="cuda")
+    for _ in range(calls):
+        kg.kg_gnm_directed(n, m, 1, P, 4, out.data_ptr(), m, s)
+    torch.cuda.synchronize()
+    kg.check_device_error()
+    print(json.dumps({"profile_config1": calls, "edges": m}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -677,6 +692,9 @@ def main():
     ap.add_argument("--profile-rgg", type=int, nargs=2, metavar=("DIM", "LOG2N"), default=None,
                     help="run only RGG(2^LOG2N, 16 neighbours) in DIM dimensions (count pass, "
                          "then two kg_rgg calls) and exit")
+    ap.add_argument("--profile-config1", type=int, default=0, metavar="CALLS",
+                    help="run only directed G(n,m) at n = 2^16, m = 2^20, 64 chunks CALLS times "
+                         "and exit")
     ap.add_argument("--profile-und-rows", type=int, default=0, metavar="RANGES",
                     help="run only undirected G(n,m) at n = m = 2^32: the chunk counts and the "
                          "first RANGES row ranges of 16 row blocks, and exit")
@@ -700,6 +718,8 @@ def main():
         return profile_rgg(kg, *args.profile_rgg)
     if args.profile_und_rows:
         return profile_und_rows(kg, args.profile_und_rows)
+    if args.profile_config1:
+        return profile_config1(kg, args.profile_config1)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
